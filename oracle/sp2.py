@@ -1,0 +1,228 @@
+"""Plain FP64 SP2 recursions (oracle; test infrastructure only).
+
+Everything here is numpy FP64 with ``@`` (dgemm) as the only library
+primitive. No blocking, fusion or reordering beyond what the equations state.
+
+Notation follows the paper (arXiv 2409.17033):
+  X_1 = alpha I + beta H                      (Eq. DM0, Sec. II)
+  X_{n+1} = (1 - sigma_n) X_n + sigma_n X_n^2  (Eq. DM0)
+  Y_1 = beta H1;  Y_{n+1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n)   (Eq. DM1)
+  backward: Y_M = A;  Y_{n-1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n), n = M..1;
+            chi = beta Y_0                    (Eq. DM2)
+  forward:  Y_1 = beta A, same recursion as Eq. DM1, chi = Y_{M+1}   (Eq. DM3)
+
+Readings where the paper is silent (the same readings the CUDA path takes):
+  * spectral bounds: Gershgorin discs (the paper only asks for "estimates" of
+    the extreme eigenvalues, Sec. II);
+  * branch choice: sigma = +1 (square) when |Tr[X^2] - N_occ| <= |Tr[2X - X^2] - N_occ|,
+    ties go to squaring; Tr[X^2] is ||X||_F^2 for symmetric X (Sec. II asks
+    for the trace of X_{n+1} closest to N_occ);
+  * stopping: with e_n = Tr[X_n] - ||X_n||_F^2 (the idempotency error,
+    sum of lambda (1 - lambda)), stop after step n >= min_iter when
+    |e_{n+1}| <= idem_tol, or when |e_{n-1}| <= floor_gate and
+    |e_{n+1}| >= |e_{n-1}| (the error stopped falling over a two-step
+    cycle: the precision floor). ``max_iter`` steps without either
+    condition is non-convergence.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+# ---------------------------------------------------------------- Sec. II
+def gershgorin_bounds(H: np.ndarray) -> tuple[float, float]:
+    """Lower and upper spectral bound estimates of symmetric H (Sec. II:
+    eps_min, eps_max), read as Gershgorin discs: H_ii -/+ sum_{j != i} |H_ij|."""
+    H = np.asarray(H, dtype=np.float64)
+    d = np.diag(H)
+    r = np.abs(H).sum(axis=1) - np.abs(d)
+    return float(np.min(d - r)), float(np.max(d + r))
+
+
+def sp2_scaling(eps_min: float, eps_max: float) -> tuple[float, float]:
+    """alpha = eps_max / (eps_max - eps_min), beta = -1 / (eps_max - eps_min)
+    (Sec. II, after Eq. DM0): maps the spectrum in reversed order onto [0, 1]."""
+    w = eps_max - eps_min
+    return eps_max / w, -1.0 / w
+
+
+def choose_sigma(t1: float, t2: float, nocc: float) -> int:
+    """Branch choice of Eq. DM0: trace after squaring is t2 = Tr[X^2], after
+    2X - X^2 it is 2 t1 - t2; pick the one closer to N_occ (ties: square)."""
+    return 1 if abs(t2 - nocc) <= abs(2.0 * t1 - t2 - nocc) else -1
+
+
+def traces(X: np.ndarray) -> tuple[float, float]:
+    """(Tr[X], Tr[X^2]) with Tr[X^2] written as sum_ij X_ij X_ji."""
+    return float(np.trace(X)), float(np.sum(X * X.T))
+
+
+def stop_now(n: int, e: list[float], idem_tol: float, floor_gate: float,
+             min_iter: int) -> bool:
+    """Stopping reading (module docstring). ``e[k]`` is the idempotency error
+    of X_{k+1}; after step n the newest entry is e[n] (X_{n+1})."""
+    if n < min_iter:
+        return False
+    if idem_tol > 0.0 and abs(e[n]) <= idem_tol:
+        return True
+    if n >= 2 and abs(e[n - 2]) <= floor_gate and abs(e[n]) >= abs(e[n - 2]):
+        return True
+    return False
+
+
+@dataclasses.dataclass
+class SP2Result:
+    D: np.ndarray                 # X_{M+1}
+    alpha: float
+    beta: float
+    sigma: list[int]              # sigma_1..sigma_M
+    errors: list[float]           # e for X_1..X_{M+1}
+    X: list[np.ndarray] | None    # X_1..X_M (inputs of each step) when kept
+    converged: bool
+
+    @property
+    def M(self) -> int:
+        return len(self.sigma)
+
+
+def sp2_density(H: np.ndarray, nocc: float, idem_tol: float = 1e-10,
+                max_iter: int = 100, min_iter: int = 4, floor_gate: float = 0.1,
+                sigma: list[int] | None = None, keep: bool = False,
+                bounds: tuple[float, float] | None = None) -> SP2Result:
+    """SP2 recursive Fermi-operator expansion, Eq. DM0.
+
+    If ``sigma`` is given, exactly those branches are taken (M = len(sigma))
+    and no stopping test is made; otherwise sigma_n comes from
+    ``choose_sigma`` and the stopping reading of the module docstring."""
+    H = np.asarray(H, dtype=np.float64)
+    n_ = H.shape[0]
+    emin, emax = gershgorin_bounds(H) if bounds is None else bounds
+    alpha, beta = sp2_scaling(emin, emax)
+    X = alpha * np.eye(n_) + beta * H
+    t1, t2 = traces(X)
+    errs = [t1 - t2]
+    sig: list[int] = []
+    hist: list[np.ndarray] | None = [] if keep else None
+    converged = False
+    steps = len(sigma) if sigma is not None else max_iter
+    for n in range(1, steps + 1):
+        s = sigma[n - 1] if sigma is not None else choose_sigma(t1, t2, nocc)
+        if keep:
+            hist.append(X)
+        X2 = X @ X
+        X = X2 if s > 0 else 2.0 * X - X2
+        sig.append(int(s))
+        t1, t2 = traces(X)
+        errs.append(t1 - t2)
+        if sigma is None and stop_now(n, errs, idem_tol, floor_gate, min_iter):
+            converged = True
+            break
+    if sigma is not None:
+        converged = True
+    return SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs,
+                     X=hist, converged=converged)
+
+
+# ---------------------------------------------------------------- Sec. III
+def _response_step(Y: np.ndarray, X: np.ndarray, s: int) -> np.ndarray:
+    """(1 - sigma) Y + sigma (Y X + X Y): the update shared by Eqs. DM1-DM3."""
+    P = Y @ X + X @ Y
+    return P if s > 0 else 2.0 * Y - P
+
+
+def dm_response(X_hist: list[np.ndarray], sigma: list[int], beta: float,
+                H1: np.ndarray) -> np.ndarray:
+    """First-order density-matrix response D^(1), Eq. DM1, over the stored
+    X_1..X_M of the ground-state run."""
+    Y = beta * np.asarray(H1, dtype=np.float64)
+    for X, s in zip(X_hist, sigma):
+        Y = _response_step(Y, X, s)
+    return Y
+
+
+# ---------------------------------------------------------------- Sec. IV
+def susceptibility_backward(X_hist: list[np.ndarray], sigma: list[int],
+                            beta: float, A: np.ndarray) -> np.ndarray:
+    """Backward (adjoint) susceptibility, Eq. DM2: start from A at n = M and
+    run the response update against X_M, X_{M-1}, ..., X_1; chi = beta Y_0."""
+    Y = np.asarray(A, dtype=np.float64)
+    for X, s in zip(reversed(X_hist), reversed(sigma)):
+        Y = _response_step(Y, X, s)
+    return beta * Y
+
+
+def susceptibility_forward(X_hist: list[np.ndarray], sigma: list[int],
+                           beta: float, A: np.ndarray) -> np.ndarray:
+    """Forward susceptibility, Eq. DM3: Eq. DM1 with A in place of H1."""
+    return dm_response(X_hist, sigma, beta, A)
+
+
+# ---------------------------------------------------------------- Appendix
+def merged_response(H: np.ndarray, nocc: float, B: np.ndarray, **kw):
+    """Merged forms of the Appendix (Eq. DMSuscept with B = A, Eq. DMPert with
+    B = H1): the response Y runs beside X in one loop, so no X_n is stored.
+    B may be one matrix or a stack (B_k). Returns (SP2Result, Y_{M+1}).
+    The branch sequence and M are the ones the ground-state loop takes."""
+    H = np.asarray(H, dtype=np.float64)
+    n_ = H.shape[0]
+    Bs = np.asarray(B, dtype=np.float64)
+    single = Bs.ndim == 2
+    if single:
+        Bs = Bs[None]
+    idem_tol = kw.get("idem_tol", 1e-10)
+    max_iter = kw.get("max_iter", 100)
+    min_iter = kw.get("min_iter", 4)
+    floor_gate = kw.get("floor_gate", 0.1)
+    sigma = kw.get("sigma")
+    emin, emax = kw.get("bounds") or gershgorin_bounds(H)
+    alpha, beta = sp2_scaling(emin, emax)
+    X = alpha * np.eye(n_) + beta * H
+    Y = [beta * b for b in Bs]
+    t1, t2 = traces(X)
+    errs = [t1 - t2]
+    sig: list[int] = []
+    converged = sigma is not None
+    steps = len(sigma) if sigma is not None else max_iter
+    for n in range(1, steps + 1):
+        s = sigma[n - 1] if sigma is not None else choose_sigma(t1, t2, nocc)
+        Y = [_response_step(y, X, s) for y in Y]
+        X2 = X @ X
+        X = X2 if s > 0 else 2.0 * X - X2
+        sig.append(int(s))
+        t1, t2 = traces(X)
+        errs.append(t1 - t2)
+        if sigma is None and stop_now(n, errs, idem_tol, floor_gate, min_iter):
+            converged = True
+            break
+    res = SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs,
+                    X=None, converged=converged)
+    Yo = np.stack(Y)
+    return res, (Yo[0] if single else Yo)
+
+
+# ---------------------------------------------------------------- contractions
+def trace_product(P: np.ndarray, Q: np.ndarray) -> float:
+    """Tr[P Q] = sum_ij P_ij Q_ji (Eqs. expectation, direct, dual)."""
+    return float(np.sum(np.asarray(P, np.float64) * np.asarray(Q, np.float64).T))
+
+
+def contract(Ps: np.ndarray, Qs: np.ndarray) -> np.ndarray:
+    """Matrix of responses out[l, k] = Tr[P_l Q_k] for stacks P (L,N,N) and
+    Q (K,N,N): a^(1) = Tr[chi^A_l H1_k] (Eq. dual) or Tr[A_l D1_k] (Eq. direct)."""
+    Ps = np.asarray(Ps, np.float64)
+    Qs = np.asarray(Qs, np.float64)
+    out = np.empty((Ps.shape[0], Qs.shape[0]))
+    for l in range(Ps.shape[0]):
+        for k in range(Qs.shape[0]):
+            out[l, k] = trace_product(Ps[l], Qs[k])
+    return out
+
+
+def contract_diag(Ps: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Same as ``contract`` for diagonal Q_k = diag(q_k): sum_i P_l,ii q_k,i."""
+    Ps = np.asarray(Ps, np.float64)
+    q = np.asarray(q, np.float64)
+    dg = np.stack([np.diag(p) for p in Ps])
+    return dg @ q.T

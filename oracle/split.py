@@ -1,0 +1,52 @@
+"""Split-precision products of Sec. VI.B (oracle; test infrastructure only).
+
+Eq. doubleHalf: X = X^(h) + X^(l) with X^(h) = half[X] and
+X^(l) = half[X - single[X^(h)]]. "half" is FP16 in the paper; the BF16 form is
+the same construction with bfloat16 as the narrow type.
+
+Eq. MixPrecMult / Eq. mults: X Y ~ X^(h) Y^(h) + X^(h) Y^(l) + X^(l) Y^(h),
+the X^(l) Y^(l) term dropped. Here the three products are formed in FP64 from
+the exactly represented narrow operands, so the only difference from a
+tensor-core evaluation with FP32 accumulation is the accumulation rounding.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round FP32 values to bfloat16 (round to nearest, ties to even), returned
+    as float32 holding the bfloat16 value. Written from the format's
+    definition: bfloat16 keeps the top 16 bits of the IEEE binary32 pattern.
+    NaN inputs are not expected here."""
+    x32 = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = x32.view(np.uint32).astype(np.uint64)
+    lsb = (b >> np.uint64(16)) & np.uint64(1)
+    r = (b + np.uint64(0x7FFF) + lsb) >> np.uint64(16)
+    out = (r << np.uint64(16)).astype(np.uint32)
+    return out.view(np.float32).reshape(x32.shape)
+
+
+def round_fp16(x: np.ndarray) -> np.ndarray:
+    """Round FP32 values to IEEE binary16 (numpy's RNE cast), as float32."""
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def split_hi_lo(x: np.ndarray, kind: str = "bf16", lo_scale: float = 1.0):
+    """Eq. doubleHalf. Returns (hi, lo) as float32 arrays holding narrow values.
+    ``lo_scale`` (a power of two) multiplies the residual before it is rounded
+    (FP16 range handling); the returned lo is the scaled one."""
+    rnd = round_bf16 if kind == "bf16" else round_fp16
+    x32 = np.asarray(x, dtype=np.float32)
+    hi = rnd(x32)
+    lo = rnd((x32 - hi) * np.float32(lo_scale))
+    return hi, lo
+
+
+def mixed_product(X: np.ndarray, Y: np.ndarray, kind: str = "bf16",
+                  lo_scale: float = 1.0) -> np.ndarray:
+    """Eq. MixPrecMult without the lo*lo term, in FP64 on the split operands."""
+    xh, xl = split_hi_lo(X, kind, lo_scale)
+    yh, yl = split_hi_lo(Y, kind, lo_scale)
+    xh, xl, yh, yl = (a.astype(np.float64) for a in (xh, xl, yh, yl))
+    return xh @ yh + (xh @ yl + xl @ yh) / lo_scale

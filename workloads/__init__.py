@@ -1,0 +1,186 @@
+"""Seeded synthetic inputs for the SP2 density / response / susceptibility path.
+
+This module only draws numbers and lays them out as matrices. It holds none of
+the method's arithmetic (no spectral bounds, no recursion, no traces), so the
+oracle and the CUDA path can both consume its output without sharing any of
+the computation they are checked on.
+
+All generators use ``numpy.random.default_rng(seed)`` (PCG64) and draw in the
+order documented in each function, so a (config, seed) pair always yields the
+same matrices on every machine.
+
+Workloads (the problem statement is the paper's Sec. II: a real symmetric
+N x N Hamiltonian H with S = I and an occupation N_occ; perturbations H1 and
+observables A are real symmetric N x N matrices, Sec. III and IV):
+
+* ``random_spectrum``: H = Q diag(e) Q^T with Q Haar-orthogonal and a gapped
+  two-band spectrum; A and H1_k symmetric Gaussian with sigma = 1/sqrt(N).
+* ``tight_binding``: sites at random positions in a periodic cube of number
+  density 0.1, 4 orbitals per site, hopping -exp(-r/1.5) for r < 6 between
+  every orbital pair of two distinct sites, onsite U[-0.3, 0.3] plus an
+  alternating +/-0.8 shift that opens a gap at half filling.
+* ``metallic_spectrum``: H = Q diag(e) Q^T with e ~ U[-1, 1] (gapless), for
+  the finite-temperature variant.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "haar_orthogonal",
+    "sym_gaussian",
+    "RandomSpectrumProblem",
+    "random_spectrum",
+    "TightBinding",
+    "tight_binding",
+    "tb_dipole_observables",
+    "tb_site_potentials",
+    "metallic_spectrum",
+]
+
+
+def haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Haar-distributed orthogonal n x n matrix: QR of an iid N(0,1) matrix,
+    with the columns' signs fixed by sign(diag R) so the law is exactly Haar.
+    Draws n*n normals (row-major)."""
+    g = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(g)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return q * s[None, :]
+
+
+def sym_gaussian(rng: np.random.Generator, n: int, sigma: float) -> np.ndarray:
+    """Symmetric matrix whose upper triangle (diagonal included) is iid
+    N(0, sigma^2), mirrored. Draws n*n normals row-major and keeps the upper
+    triangle, so the draw count does not depend on the layout."""
+    g = rng.standard_normal((n, n)) * sigma
+    u = np.triu(g)
+    return u + np.triu(u, 1).T
+
+
+@dataclasses.dataclass
+class RandomSpectrumProblem:
+    H: np.ndarray          # (N, N) float64, symmetric
+    Q: np.ndarray          # (N, N) eigenvectors (columns)
+    e: np.ndarray          # (N,) eigenvalues, H = Q diag(e) Q^T
+    A: np.ndarray          # (N, N) observable
+    H1: np.ndarray         # (K, N, N) perturbations
+    nocc: int
+
+
+def random_spectrum(n: int = 128, nocc: int | None = None, k: int = 8,
+                    lo=(-1.0, -0.2), hi=(0.2, 1.0), seed: int = 0) -> RandomSpectrumProblem:
+    """Gapped random-spectrum problem.
+
+    Draw order: Q (n*n normals), then nocc eigenvalues U[lo], then n-nocc
+    eigenvalues U[hi], then A (n*n normals), then H1_k for k = 0..K-1
+    (n*n normals each). sigma = 1/sqrt(n) for A and H1_k."""
+    if nocc is None:
+        nocc = n // 2
+    rng = np.random.default_rng(seed)
+    q = haar_orthogonal(rng, n)
+    e = np.concatenate([rng.uniform(lo[0], lo[1], nocc),
+                        rng.uniform(hi[0], hi[1], n - nocc)])
+    h = (q * e[None, :]) @ q.T
+    h = 0.5 * (h + h.T)
+    sig = 1.0 / math.sqrt(n)
+    a = sym_gaussian(rng, n, sig)
+    h1 = np.stack([sym_gaussian(rng, n, sig) for _ in range(k)]) if k else np.zeros((0, n, n))
+    return RandomSpectrumProblem(H=h, Q=q, e=e, A=a, H1=h1, nocc=nocc)
+
+
+@dataclasses.dataclass
+class TightBinding:
+    H: np.ndarray          # (N, N) float64
+    pos: np.ndarray        # (n_sites, 3) site positions in [0, L)^3
+    box: float             # cube edge L
+    norb: int              # orbitals per site
+    nocc: int
+
+    @property
+    def n(self) -> int:
+        return self.H.shape[0]
+
+
+def _tb_hopping(pos: np.ndarray, box: float, rcut: float, decay: float,
+                norb: int, out: np.ndarray) -> None:
+    """Adds -exp(-r/decay) to every orbital pair of every pair of distinct
+    sites closer than rcut (minimum-image distance in the periodic cube)."""
+    ns = pos.shape[0]
+    chunk = 512
+    for s0 in range(0, ns, chunk):
+        s1 = min(ns, s0 + chunk)
+        d = pos[s0:s1, None, :] - pos[None, :, :]
+        d -= box * np.round(d / box)
+        r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+        for ia in range(s1 - s0):
+            a = s0 + ia
+            nb = np.nonzero((r[ia] < rcut))[0]
+            nb = nb[nb != a]
+            if nb.size == 0:
+                continue
+            t = -np.exp(-r[ia, nb] / decay)
+            rows = slice(a * norb, (a + 1) * norb)
+            blk = np.repeat(t, norb)[None, :]           # (1, nb*norb)
+            cols = (nb[:, None] * norb + np.arange(norb)[None, :]).reshape(-1)
+            out[rows, cols] += blk
+
+
+def tight_binding(n: int, seed: int = 0, norb: int = 4, density: float = 0.1,
+                  rcut: float = 6.0, decay: float = 1.5, onsite: float = 0.3,
+                  stagger: float = 0.8, dtype=np.float64) -> TightBinding:
+    """Dense-stored tight-binding Hamiltonian.
+
+    n_sites = n / norb sites at positions U[0, L)^3 with L = (n_sites/density)^(1/3).
+    Draw order: positions (n_sites*3 uniforms, row-major), then onsite energies
+    (n uniforms, one per orbital). Orbital g (global index) gets
+    U[-onsite, onsite] + stagger * (-1)^g on the diagonal. N_occ = n / 2."""
+    assert n % norb == 0
+    ns = n // norb
+    rng = np.random.default_rng(seed)
+    box = (ns / density) ** (1.0 / 3.0)
+    pos = rng.uniform(0.0, box, (ns, 3))
+    eps = rng.uniform(-onsite, onsite, n) + stagger * np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    h = np.zeros((n, n), dtype=dtype)
+    _tb_hopping(pos, box, rcut, decay, norb, h)
+    h[np.arange(n), np.arange(n)] += eps
+    return TightBinding(H=h, pos=pos, box=box, norb=norb, nocc=n // 2)
+
+
+def tb_dipole_observables(tb: TightBinding) -> np.ndarray:
+    """Four diagonal observables (returned as their diagonals, shape (4, N)):
+    the x, y, z coordinates of each orbital's site relative to the box centre
+    (dipole-like), and the population of site 0 (indicator of its orbitals)."""
+    n = tb.n
+    c = np.repeat(tb.pos - 0.5 * tb.box, tb.norb, axis=0)      # (N, 3)
+    pop = np.zeros(n)
+    pop[:tb.norb] = 1.0
+    return np.stack([c[:, 0], c[:, 1], c[:, 2], pop])
+
+
+def tb_site_potentials(tb: TightBinding, k: int, seed: int = 1) -> np.ndarray:
+    """K random site-potential perturbations, returned as diagonals (K, N):
+    each site's potential is U[-1, 1], shared by its orbitals. Draw order:
+    K * n_sites uniforms, row-major."""
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-1.0, 1.0, (k, tb.n // tb.norb))
+    return np.repeat(v, tb.norb, axis=1)
+
+
+def metallic_spectrum(n: int = 8192, k: int = 256, seed: int = 0) -> RandomSpectrumProblem:
+    """Gapless problem: e ~ U[-1, 1], Haar Q, A and H1_k symmetric
+    N(0, 1/n). Draw order: Q, e (n uniforms), A, H1_k. nocc is n/2 (a
+    nominal count; the finite-temperature variant fixes mu = 0)."""
+    rng = np.random.default_rng(seed)
+    q = haar_orthogonal(rng, n)
+    e = rng.uniform(-1.0, 1.0, n)
+    h = (q * e[None, :]) @ q.T
+    h = 0.5 * (h + h.T)
+    sig = 1.0 / math.sqrt(n)
+    a = sym_gaussian(rng, n, sig)
+    h1 = np.stack([sym_gaussian(rng, n, sig) for _ in range(k)]) if k else np.zeros((0, n, n))
+    return RandomSpectrumProblem(H=h, Q=q, e=e, A=a, H1=h1, nocc=n // 2)
