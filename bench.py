@@ -1,0 +1,368 @@
+"""Benchmark: forward SP2 + adjoint susceptibility at N = 16384 on one GB300.
+
+One step = one full solve of the hot path on a seeded synthetic tight-binding
+Hamiltonian (4096 sites x 4 orbitals, N_occ = 8192): the SP2 density of
+Eq. DM0 with split-precision (BF16 hi/lo, FP32 accumulation) tensor-core
+products, X_n checkpointed every 4 steps, then the adjoint recursion of
+Eq. DM2 seeded with the x-dipole observable, recomputing each segment of X_n
+from its checkpoint. Output: D and chi^A.
+
+Prints ONE JSON line (rank 0). Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch one process per GPU with torch.distributed.run; each rank
+solves its own seeded problem (independent units, weak scaling, no
+collective on the data path; a barrier and a max-reduce of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N=16384 fwd+adjoint chi: ms, TFLOP/s, %TC peak, rel err vs FP64; mixed vs plain"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")
+TC_SOURCE = os.path.join(ROOT, "paper_2409_17033_gb300", "csrc", "gemm_tc.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--ckpt-k", type=int, default=4)
+    ap.add_argument("--mode", default="bf16x2")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(n: int, seed: int):
+    import workloads
+    tb = workloads.tight_binding(n, seed=seed, dtype=np.float32)
+    A = workloads.tb_dipole_observables(tb)[0:1].astype(np.float32)  # x-dipole, diagonal
+    return tb, A
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def traffic_per_launch(n: int):
+    """DRAM bytes per product launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+        src = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
+        if d.get("kernel_sha256") != src:
+            return None
+        return float(d["bytes_per_launch_at_n"][str(n)])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.out = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=self.out, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            txt, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            txt = ""
+        rows = []
+        for line in txt.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def gpu_uuid():
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def logical_flops(n: int, m: int, k: int) -> float:
+    """Logical products of one solve, each 2 N^3: M squares forward, the
+    M - ceil(M/k) recomputed squares and M adjoint products Y X (X Y is its
+    transpose)."""
+    recompute = m - (m + k - 1) // k
+    return (m + recompute + m) * 2.0 * float(n) ** 3
+
+
+def cpu_oracle_sample(n: int, H32: np.ndarray, nocc: float):
+    """One SP2 step of the FP64 oracle at full size (one N^3 product), timed."""
+    from oracle import sp2 as osp2
+    H = H32.astype(np.float64)
+    t0 = time.perf_counter()
+    osp2.sp2_density(H, nocc, sigma=[1])
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * float(n) ** 3 / dt / 1e12
+
+
+def run_reference(args, ws, rank):
+    """The oracle as it stands on the host cores, on this workload: each step
+    is one FP64 SP2 step (one N x N x N product) at N = args.n."""
+    if rank != 0:
+        return
+    tb, A = workload(args.n, seed=0)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args.n, tb.H, tb.nocc)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = cpu_oracle_sample(args.n, tb.H, tb.nocc)
+        times.append(dt)
+    t = sum(times) / len(times)
+    val = 2.0 * float(args.n) ** 3 / t / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"tight-binding N={args.n}, FP64 oracle, one SP2 step (one N^3 product) per step",
+                   "n": args.n},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"one FP64 SP2 step at N={args.n} per step (numpy/BLAS, all host threads)"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank):
+    import torch
+
+    import paper_2409_17033_gb300 as sp2
+
+    dev = torch.cuda.current_device()
+    tb, A = workload(args.n, seed=rank)
+    n = args.n
+    H = torch.from_numpy(tb.H).cuda()
+    Ad = torch.from_numpy(A).cuda()
+    h = sp2.Handle()
+    kw = dict(direction="backward", diag_only=True, mode=args.mode, want_density=True,
+              ckpt_k=args.ckpt_k, handle=h)
+
+    def step(timing=False):
+        return sp2.sp2_susceptibility(H, tb.nocc, Ad, time_kernels=timing, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(gpu_uuid())
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        chi, D, info = step(timing=True)
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = allmax(ws, ms)
+    info = infos[-1]
+    M = info["M"]
+    lflops = logical_flops(n, M, args.ckpt_k)
+    value = ws * lflops / (ms_max * 1e-3) / 1e12
+    exec_tflops = info["executed_flops"] / (ms * 1e-3) / 1e12
+    pk, pk_kind = peaks()
+    # dominant kernel: the tcgen05 product kernel, timed by events around each launch
+    prod_ms = statistics.mean(i["product_ms"] for i in infos)
+    prod_launch = statistics.mean(i["product_launches_timed"] for i in infos)
+    alg = statistics.mean(i["algorithmic_flops"] for i in infos)
+    achieved = alg / (prod_ms * 1e-3) / 1e12
+    peak = pk["bf16_tflops_sustained"]
+    traffic = traffic_per_launch(n)
+    gpu_launches = sum(i["kernel_launches"] for i in infos)
+
+    quality = {
+        "M": M, "trace_err": abs(info["trace"] - tb.nocc), "idem_err": info["idem_err"],
+        "product_time_share": prod_ms / ms,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x2 (split bf16 products, f32 accumulate/master)",
+        "data": "synthetic",
+        "config": {
+            "workload": (f"tight-binding N={n} ({n // 4} sites x 4 orbitals, density 0.1, r<6), "
+                         f"N_occ={tb.nocc}: forward SP2 (Eq. DM0) + adjoint chi (Eq. DM2) of the "
+                         f"x-dipole, X_n checkpointed every {args.ckpt_k} steps"),
+            "n": n, "mode": args.mode, "ckpt_k": args.ckpt_k, "global_batch": ws,
+            "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (each N x N FP32 matrix is 1 GiB)",
+        },
+        "ms_per_solve": ms_max, "tflops_effective": value / ws, "tflops_executed": exec_tflops,
+        "tc_peak_frac_executed": exec_tflops / peak,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_gemm_tc (tcgen05 split-BF16 product)",
+                     "launches_per_step": prod_launch,
+                     "peak_kind": f"bf16_tflops_sustained ({pk_kind})"},
+        "quality": quality,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+
+    # plain forms on the same GPU: per-product timings of the FP32 CUDA-core
+    # kernels extrapolated to this solve's product count (stated as such)
+    if not args.no_plain and rank == 0:
+        try:
+            H64 = H
+            _, inf_sq = sp2.sp2_density(H64, tb.nocc, mode="fp32", sigma=[1], time_kernels=True,
+                                        handle=h)
+            _, _, inf_y = sp2.sp2_susceptibility(H64, tb.nocc, Ad, "forward", diag_only=True,
+                                                 mode="fp32", sigma=[1], time_kernels=True, handle=h)
+            sq_ms = inf_sq["product_ms"]
+            y_ms = inf_y["product_ms"] - sq_ms
+            rec = M - (M + args.ckpt_k - 1) // args.ckpt_k
+            est = (M + rec) * sq_ms + M * max(y_ms, 0.0)
+            line["plain_fp32"] = {"ms_per_solve_extrapolated": est,
+                                  "tflops_effective": lflops / (est * 1e-3) / 1e12,
+                                  "square_ms": sq_ms, "response_product_ms": y_ms,
+                                  "note": "FP32 CUDA-core products, per-product event times x product count"}
+        except Exception as ex:  # report, do not hide
+            line["plain_fp32"] = {"error": str(ex)}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    if not args.no_e2e:
+        Hh = torch.from_numpy(tb.H).pin_memory().numpy()
+        Ah = torch.from_numpy(A).pin_memory().numpy()
+        hh = sp2.Handle()
+        kwh = dict(kw)
+        kwh["handle"] = hh
+        sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            chi_h, D_h, _ = sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e_s = allmax(ws, e2e_s)
+        line["e2e"] = {"value": ws * lflops / e2e_s / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": int(Hh.nbytes + Ah.nbytes),
+                       "d2h_bytes_per_step": int(chi_h.nbytes + D_h.nbytes),
+                       "ms_per_step": e2e_s * 1e3}
+        del hh
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        dt, tf = cpu_oracle_sample(n, tb.H, tb.nocc)
+        line["cpu_baseline"] = {"value": tf, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": (f"one FP64 oracle SP2 step (one N^3 product) at N={n}, "
+                                           f"{dt:.1f} s; numpy/BLAS on all host threads"),
+                                "ms_per_solve_extrapolated": dt * 1e3 * lflops / (2.0 * n ** 3)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = (1, 0, 0)
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, ws, rank)
+        return
+    ws, rank, local = dist_setup()
+    run_ours(args, ws, rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * sp2.h -- C ABI of the GB300 SP2 density-matrix / response / susceptibility
+ * library (libsp2.so).
+ *
+ * The operations follow A. M. N. Niklasson et al., "Susceptibility Formulation
+ * of Density Matrix Perturbation Theory" (arXiv 2409.17033):
+ *
+ *   sp2_density        Eq. DM0 (Sec. II): D = theta(mu I - H) by the SP2
+ *                      recursive Fermi-operator expansion, Tr[D] = N_occ.
+ *   sp2_response       Eq. DMPert (Appendix; Eq. DM1 merged with Eq. DM0):
+ *                      first-order density-matrix responses D1_k to a batch
+ *                      of Hamiltonian perturbations H1_k.
+ *   sp2_susceptibility Eq. DMSuscept (Appendix; Eq. DM3 merged with Eq. DM0),
+ *                      forward, or Eq. DM2 (Sec. IV.A), backward/adjoint over
+ *                      the stored or recomputed X_n: chi^A_l of a batch of
+ *                      observables A_l, chi^A_ij = d Tr[A D] / d H_ij (Eq. Suscept).
+ *   sp2_adjoint        Eq. DM2 on the X_n history kept by the handle's last
+ *                      sp2_density call (the backward pass of an autograd
+ *                      wrapper: grad_H = chi^G for the incoming gradient G).
+ *   response_contract  a1[l,k] = Tr[P_l Q_k] (Eqs. expectation, direct, dual):
+ *                      Tr[chi^A_l H1_k] or Tr[A_l D1_k], accumulated in FP64.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Matrices are dense, square N x N, row-major and contiguous; a batch of B
+ * matrices is B*N*N contiguous elements. H, H1_k, A_l must be symmetric (the
+ * paper assumes S = I and symmetric operators, Sec. I); symmetry is not
+ * checked. The element type of every caller matrix is given by `dtype`
+ * (SP2_F64 = double, SP2_F32 = float); `out` of response_contract is always
+ * double.
+ *
+ * Pointers may be device memory (cudaMalloc, torch tensors) or host memory
+ * (pageable or pinned); host buffers are staged through handle-owned device
+ * memory with copies on the handle's stream, and the call then returns only
+ * after the result is back in host memory. The library never frees or keeps
+ * caller memory. All device work is enqueued on the handle's stream; when
+ * every buffer is device memory the call still synchronises that stream
+ * once per SP2 iteration batch (it reads the branch/stop state), so results
+ * are complete when the call returns.
+ *
+ * Internal working storage (padded copies, X ping-pong buffers, split planes,
+ * the X_n checkpoints of the adjoint, reduction partials) is owned by the
+ * handle, grows on demand up to `workspace_limit_bytes` (0 = no limit) and is
+ * freed by sp2_destroy.
+ *
+ * Return value: an sp2_status. On failure nothing is guaranteed about the
+ * outputs; sp2_last_error(h) gives a message (handle-owned string, valid
+ * until the next call on that handle). No exception crosses the ABI.
+ * A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef SP2_H
+#define SP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SP2_MAX_ITER 256
+
+typedef enum {
+  SP2_OK = 0,
+  SP2_EINVAL = 1,      /* bad argument (null pointer, negative size, bad enum, N_occ out of [0,N]) */
+  SP2_ENOMEM = 2,      /* device allocation failed or workspace limit exceeded */
+  SP2_ENOCONV = 3,     /* max_iter steps without meeting the stop rule (outputs hold the last iterate) */
+  SP2_ENONFINITE = 4,  /* NaN/Inf in the spectral bounds or traces (non-finite input) */
+  SP2_ETIMEOUT = 5,    /* a device-side wait hit its time limit; the kernel bailed out */
+  SP2_ECUDA = 6,       /* a CUDA runtime/driver call failed (message has the CUDA error) */
+  SP2_ENOTIMPL = 7,    /* combination not implemented */
+  SP2_ENOSTATE = 8     /* sp2_adjoint without a kept X_n history on this handle */
+} sp2_status;
+
+typedef enum { SP2_F64 = 0, SP2_F32 = 1 } sp2_dtype;
+
+/* Arithmetic of the matrix products (Sec. VI.B).
+ *   SP2_MODE_FP64    plain FP64 (CUDA-core DFMA).
+ *   SP2_MODE_FP32    plain FP32 (CUDA-core FFMA): the paper's "GPU FP32" form.
+ *   SP2_MODE_BF16X2  Eq. doubleHalf / Eq. MixPrecMult with bfloat16 hi/lo planes:
+ *                    three tensor-core products (hi*hi + hi*lo + lo*hi, lo*lo
+ *                    dropped, Eq. mults), FP32 accumulation, FP32 master copy.
+ */
+typedef enum {
+  SP2_MODE_FP64 = 0,
+  SP2_MODE_FP32 = 1,
+  SP2_MODE_BF16X2 = 2
+} sp2_mode;
+
+typedef struct {
+  int mode;            /* sp2_mode */
+  double idem_tol;     /* stop when |e_{n+1}| <= idem_tol; <= 0 disables this test.
+                          e_n = Tr[X_n] - ||X_n||_F^2 is the idempotency error (Sec. II). */
+  double floor_gate;   /* precision-floor stop: after step n, stop when |e_{n-1}| <= floor_gate
+                          and |e_{n+1}| >= |e_{n-1}|; < 0 selects the default 0.1, 0 disables */
+  int max_iter;        /* cap on SP2 steps M (1..SP2_MAX_ITER; 0 = default 100) */
+  int min_iter;        /* no stop test before this step (default 4 when < 0) */
+  int fixed_m;         /* > 0: take exactly fixed_m steps with the branches in sigma_in */
+  const int8_t* sigma_in; /* host array of fixed_m branch signs (+1 square, -1 2X-X^2) */
+  double eps_min;      /* if eps_min < eps_max: spectral bounds to use instead of the */
+  double eps_max;      /* Gershgorin estimate (Sec. II: alpha, beta from eps_min/eps_max) */
+  int ckpt_k;          /* sp2_density keep_history / backward chi: keep X_n every ckpt_k
+                          steps (1 = all), recompute the rest per segment (0 = default 4) */
+  int keep_history;    /* sp2_density: keep the X_n checkpoints for a later sp2_adjoint */
+  int time_kernels;    /* 1: bracket every product-kernel launch with CUDA events on the
+                          handle's stream and report their summed duration in sp2_info */
+} sp2_opts;
+
+typedef struct {
+  int M;               /* SP2 steps taken */
+  int converged;       /* 1 if a stop rule fired (or fixed_m given) */
+  double alpha, beta;  /* X_1 = alpha I + beta H */
+  double eps_min, eps_max;
+  double trace;        /* Tr[D] in FP64 */
+  double idem_err;     /* e of D = X_{M+1} */
+  int8_t sigma[SP2_MAX_ITER];         /* sigma_1..sigma_M */
+  double errors[SP2_MAX_ITER + 1];    /* e of X_1..X_{M+1} */
+  int64_t n_gemm_launches;            /* product-kernel launches that did work */
+  double executed_flops;              /* tensor/FMA flops issued by the product kernels (FMA = 2) */
+  double algorithmic_flops;           /* flops the products need by definition: the upper
+                                         triangle (with diagonal) of X^2, all of Y X, on the
+                                         caller's N (not the padding), x3 for the split form */
+  int64_t kernel_launches;            /* every kernel this call launched (no-op launches included) */
+  double product_ms;                  /* time_kernels: summed event time of the product launches
+                                         that did work, else 0 */
+  int64_t product_launches_timed;
+} sp2_info;
+
+typedef struct sp2_handle_s* sp2_handle_t;
+
+/* Fill *opts with defaults (mode FP32, idem_tol 0, floor_gate 0.1, max_iter 100, min_iter 4). */
+void sp2_default_opts(sp2_opts* opts);
+
+/* Create a handle bound to the current CUDA device and `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream). Returns SP2_EINVAL for a null
+ * out-pointer, SP2_ECUDA if no device is usable. */
+int sp2_create(sp2_handle_t* out, void* cuda_stream, size_t workspace_limit_bytes);
+int sp2_destroy(sp2_handle_t h);
+int sp2_set_stream(sp2_handle_t h, void* cuda_stream);
+const char* sp2_last_error(sp2_handle_t h);
+/* Bytes of device memory the handle currently holds. */
+size_t sp2_workspace_bytes(sp2_handle_t h);
+
+/* Eq. DM0. H: N x N input. nocc: N_occ in [0, N]. D: N x N output.
+ * info (nullable, host): M, branch sequence, errors, alpha/beta. */
+int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc,
+                const sp2_opts* opts, void* D, sp2_info* info);
+
+/* Eq. DMPert: K first-order responses D1_k (K x N x N) to H1_k. If
+ * h1_diag_only != 0, H1 holds only the K diagonals (K x N), i.e.
+ * H1_k = diag(H1[k, :]). D (nullable) receives D^(0). K = 0 is allowed. */
+int sp2_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc,
+                 const void* H1, int64_t K, int h1_diag_only, const sp2_opts* opts,
+                 void* D, void* D1, sp2_info* info);
+
+/* Susceptibilities chi^A_l (L x N x N) of L observables A_l.
+ * direction 0: forward, Eq. DMSuscept (X_n generated on the fly, nothing stored).
+ * direction 1: backward, Eq. DM2, X_n kept every opts->ckpt_k steps and the
+ *              rest recomputed segment by segment.
+ * a_diag_only != 0: A holds only the L diagonals (L x N). D (nullable) receives D^(0). */
+int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc,
+                       const void* A, int64_t L, int a_diag_only, int direction,
+                       const sp2_opts* opts, void* D, void* chi, sp2_info* info);
+
+/* Eq. DM2 against the X_n history kept by the last sp2_density(keep_history=1)
+ * on this handle: G (N x N, symmetric, dtype of that call) -> grad (N x N) with
+ * grad = d Tr[G D] / d H. SP2_ENOSTATE if no history is kept or N differs. */
+int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad, sp2_info* info);
+
+/* Release a kept X_n history (device memory) without destroying the handle. */
+int sp2_release_history(sp2_handle_t h);
+
+/* out[l*K + k] = sum_ij P_l[i,j] * Q_k[i,j] (= Tr[P_l Q_k] for symmetric P_l or Q_k),
+ * accumulated in FP64. P: L x N x N. Q: K x N x N, or K x N diagonals when
+ * q_diag_only != 0 (then out = sum_i P_l[i,i] Q_k[i]). out: L*K doubles
+ * (device or host). L or K = 0 is allowed (nothing written). */
+int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, int64_t K,
+                      int64_t N, int dtype, int q_diag_only, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP2_H */

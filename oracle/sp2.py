@@ -43,7 +43,12 @@ def gershgorin_bounds(H: np.ndarray) -> tuple[float, float]:
 
 def sp2_scaling(eps_min: float, eps_max: float) -> tuple[float, float]:
     """alpha = eps_max / (eps_max - eps_min), beta = -1 / (eps_max - eps_min)
-    (Sec. II, after Eq. DM0): maps the spectrum in reversed order onto [0, 1]."""
+    (Sec. II, after Eq. DM0): maps the spectrum in reversed order onto [0, 1].
+    A point spectrum (eps_min == eps_max, e.g. H = c I or N = 1) has no width
+    to divide by; any interval around it does, and [eps - 1/2, eps + 1/2] is
+    the one taken (X_1 = I/2)."""
+    if not eps_max > eps_min:
+        eps_min, eps_max = eps_min - 0.5, eps_max + 0.5
     w = eps_max - eps_min
     return eps_max / w, -1.0 / w
 
@@ -67,7 +72,7 @@ def stop_now(n: int, e: list[float], idem_tol: float, floor_gate: float,
         return False
     if idem_tol > 0.0 and abs(e[n]) <= idem_tol:
         return True
-    if n >= 2 and abs(e[n - 2]) <= floor_gate and abs(e[n]) >= abs(e[n - 2]):
+    if n >= 2 and floor_gate > 0.0 and abs(e[n - 2]) <= floor_gate and abs(e[n]) >= abs(e[n - 2]):
         return True
     return False
 

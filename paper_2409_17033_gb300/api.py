@@ -1,0 +1,226 @@
+"""Python binding of libsp2.so: the C entry points under the same names.
+
+Argument marshalling only. Every step of the SP2 path runs in the library's
+CUDA kernels; this module turns torch tensors (device buffers) or numpy
+arrays (host buffers, staged by the library) into pointers and sizes, and
+allocates outputs of the matching kind. PyTorch provides device memory and the
+current stream.
+
+Functions (see include/sp2.h for the exact semantics):
+  sp2_density(H, nocc, ...)                     Eq. DM0               -> (D, info)
+  sp2_response(H, nocc, H1, ...)                Eq. DMPert (DM1)      -> (D1, D, info)
+  sp2_susceptibility(H, nocc, A, direction=...) Eq. DMSuscept / DM2   -> (chi, D, info)
+  sp2_adjoint(G, handle)                        Eq. DM2 on kept X_n   -> grad
+  response_contract(P, Q, diag_only=...)        Tr[P_l Q_k]           -> (L, K) float64
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+__all__ = ["Handle", "make_opts", "sp2_density", "sp2_response", "sp2_susceptibility",
+           "sp2_adjoint", "response_contract", "SP2Error"]
+
+SP2Error = L.SP2Error
+
+
+def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: float = -1.0,
+              max_iter: int = 0, min_iter: int = -1, sigma=None, bounds=None, ckpt_k: int = 0,
+              keep_history: bool = False, time_kernels: bool = False):
+    """sp2_opts with the library defaults for everything not given. Returns
+    (opts, keepalive) where keepalive holds the branch array referenced by
+    opts.sigma_in."""
+    lib = L.load()
+    o = L.Opts()
+    lib.sp2_default_opts(C.byref(o))
+    o.mode = L.MODES[mode] if isinstance(mode, str) else int(mode)
+    o.idem_tol = float(idem_tol)
+    o.floor_gate = float(floor_gate)
+    o.max_iter = int(max_iter)
+    o.min_iter = int(min_iter)
+    o.ckpt_k = int(ckpt_k)
+    o.keep_history = 1 if keep_history else 0
+    o.time_kernels = 1 if time_kernels else 0
+    keep = None
+    if sigma is not None:
+        arr = (C.c_int8 * max(1, len(sigma)))(*[int(s) for s in sigma])
+        o.fixed_m = len(sigma)
+        o.sigma_in = C.cast(arr, C.POINTER(C.c_int8))
+        keep = arr
+    if bounds is not None:
+        o.eps_min, o.eps_max = float(bounds[0]), float(bounds[1])
+    return o, keep
+
+
+def _dtype_code(x) -> int:
+    dt = x.dtype
+    if dt in (torch.float64, np.float64):
+        return L.F64
+    if dt in (torch.float32, np.float32):
+        return L.F32
+    raise TypeError(f"unsupported element type {dt}: float64 or float32 expected")
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        if not x.is_cuda:
+            raise ValueError("torch tensors must live on a CUDA device (use numpy arrays for host buffers)")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"expected a torch.Tensor or numpy.ndarray, got {type(x)}")
+
+
+def _empty_like(x, shape):
+    if isinstance(x, torch.Tensor):
+        return torch.empty(shape, dtype=x.dtype, device=x.device)
+    return np.empty(shape, dtype=x.dtype)
+
+
+class Handle:
+    """Owns an sp2 handle (workspace, kept X_n history) on the current device."""
+
+    def __init__(self, workspace_limit: int = 0):
+        self.lib = L.load()
+        self.h = C.c_void_p()
+        stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        rc = self.lib.sp2_create(C.byref(self.h), C.c_void_p(stream), C.c_size_t(workspace_limit))
+        if rc != L.OK:
+            raise L.SP2Error(rc, "sp2_create failed (no usable CUDA device?)")
+
+    def bind_stream(self):
+        if torch.cuda.is_available():
+            self.lib.sp2_set_stream(self.h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def check(self, rc: int, allow_noconv: bool = False):
+        if rc == L.OK or (allow_noconv and rc == L.ENOCONV):
+            return
+        raise L.SP2Error(rc, self.lib.sp2_last_error(self.h).decode())
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.sp2_workspace_bytes(self.h))
+
+    def release_history(self):
+        self.lib.sp2_release_history(self.h)
+
+    def close(self):
+        if self.h:
+            self.lib.sp2_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default: dict = {}
+
+
+def default_handle() -> Handle:
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else -1
+    h = _default.get(dev)
+    if h is None:
+        h = Handle()
+        _default[dev] = h
+    return h
+
+
+def sp2_density(H, nocc: float, mode="bf16x2", out=None, handle: Handle | None = None,
+                allow_noconv: bool = False, **kw):
+    """D = theta(mu I - H) by SP2 (Eq. DM0). H: (N, N) float64/float32, torch
+    CUDA tensor or numpy array. Returns (D, info dict)."""
+    h = handle or default_handle()
+    h.bind_stream()
+    n = H.shape[0]
+    D = out if out is not None else _empty_like(H, (n, n))
+    opts, _keep = make_opts(mode, **kw)
+    info = L.Info()
+    rc = h.lib.sp2_density(h.h, _ptr(H), n, _dtype_code(H), float(nocc), C.byref(opts), _ptr(D),
+                           C.byref(info))
+    h.check(rc, allow_noconv)
+    return D, info.to_dict()
+
+
+def sp2_response(H, nocc: float, H1, diag_only: bool = False, mode="bf16x2",
+                 want_density: bool = False, handle: Handle | None = None,
+                 allow_noconv: bool = False, **kw):
+    """First-order responses D1_k to H1_k (Eq. DMPert). H1: (K, N, N), or
+    (K, N) diagonals with diag_only=True. Returns (D1, D or None, info)."""
+    h = handle or default_handle()
+    h.bind_stream()
+    n = H.shape[0]
+    k = H1.shape[0]
+    D1 = _empty_like(H, (k, n, n))
+    D = _empty_like(H, (n, n)) if want_density else None
+    opts, _keep = make_opts(mode, **kw)
+    info = L.Info()
+    rc = h.lib.sp2_response(h.h, _ptr(H), n, _dtype_code(H), float(nocc), _ptr(H1), k,
+                            1 if diag_only else 0, C.byref(opts), _ptr(D), _ptr(D1), C.byref(info))
+    h.check(rc, allow_noconv)
+    return D1, D, info.to_dict()
+
+
+def sp2_susceptibility(H, nocc: float, A, direction: str = "forward", diag_only: bool = False,
+                       mode="bf16x2", want_density: bool = False, handle: Handle | None = None,
+                       allow_noconv: bool = False, **kw):
+    """chi^A_l for observables A_l (L, N, N) or diagonals (L, N): forward
+    Eq. DMSuscept, or backward Eq. DM2 with checkpointed X_n. Returns (chi, D or None, info)."""
+    h = handle or default_handle()
+    h.bind_stream()
+    n = H.shape[0]
+    l = A.shape[0]
+    chi = _empty_like(H, (l, n, n))
+    D = _empty_like(H, (n, n)) if want_density else None
+    opts, _keep = make_opts(mode, **kw)
+    info = L.Info()
+    d = {"forward": 0, "backward": 1}[direction]
+    rc = h.lib.sp2_susceptibility(h.h, _ptr(H), n, _dtype_code(H), float(nocc), _ptr(A), l,
+                                  1 if diag_only else 0, d, C.byref(opts), _ptr(D), _ptr(chi),
+                                  C.byref(info))
+    h.check(rc, allow_noconv)
+    return chi, D, info.to_dict()
+
+
+def sp2_adjoint(G, handle: Handle):
+    """Eq. DM2 for the symmetric part of G against the X_n history kept by the
+    handle's last sp2_density(keep_history=True). Returns d Tr[G D]/dH."""
+    h = handle
+    h.bind_stream()
+    n = G.shape[0]
+    out = _empty_like(G, (n, n))
+    info = L.Info()
+    rc = h.lib.sp2_adjoint(h.h, _ptr(G), n, _dtype_code(G), _ptr(out), C.byref(info))
+    h.check(rc)
+    return out
+
+
+def response_contract(P, Q, diag_only: bool = False, handle: Handle | None = None):
+    """out[l, k] = sum_ij P_l[i,j] Q_k[i,j] in FP64 (Tr[chi_l H1_k] / Tr[A_l D1_k]).
+    P: (L, N, N); Q: (K, N, N) or (K, N) diagonals. Returns an (L, K) float64
+    array of the same kind (torch CUDA tensor or numpy) as P."""
+    h = handle or default_handle()
+    h.bind_stream()
+    l, n = P.shape[0], P.shape[-1]
+    k = Q.shape[0]
+    if isinstance(P, torch.Tensor):
+        out = torch.empty((l, k), dtype=torch.float64, device=P.device)
+    else:
+        out = np.empty((l, k), dtype=np.float64)
+    if P.dtype != Q.dtype:
+        raise TypeError("P and Q must have the same element type")
+    rc = h.lib.response_contract(h.h, _ptr(P), l, _ptr(Q), k, n, _dtype_code(P),
+                                 1 if diag_only else 0, _ptr(out))
+    h.check(rc)
+    return out

@@ -1,0 +1,433 @@
+// Split-precision tensor-core product kernel for sm_103a (tcgen05 + TMEM + TMA).
+//
+// Computes C = A X for the SP2 path with the hi/lo splitting of Eq. doubleHalf
+// and the three-product form of Eq. MixPrecMult / Eq. mults (lo*lo dropped):
+//     A X ~ A_hi X_hi + A_hi X_lo + A_lo X_hi,
+// evaluated as ONE accumulation over a concatenated K axis of length 3 np,
+//     [A_hi | A_hi | A_lo] . [X_hi ; X_lo ; X_hi],
+// into an FP32 accumulator in tensor memory. X is symmetric, so the row-major
+// X planes are directly the K-major B operand.
+//
+// CTA tile 128 x 256, K step 64 (one 128-byte swizzle row of bf16), 4-stage
+// TMA -> shared-memory ring guarded by mbarriers. Warp roles:
+//   warp 0  (one thread)  TMA producer
+//   warp 1  (one thread)  tcgen05.mma issuer; the whole warp owns the TMEM allocation
+//   warps 2-5             epilogue: tcgen05.ld of the accumulator (warp w reads
+//                         TMEM lanes 32*(w%4) .. +31), fused SP2 branch update
+//                         (EPI_SQUARE: sigma>0 ? C : 2X - C, FP32 master + bf16
+//                         hi/lo planes written for (i,j) and mirrored to (j,i),
+//                         FP64 trace partials) or a plain FP32 store (EPI_PLAIN).
+// Every mbarrier wait is bounded in time; on expiry the CTA raises the
+// state's abort flag, waits (bounded) for its own copies in flight and
+// returns after freeing its TMEM, and later CTAs exit at once.
+#include <cuda.h>
+
+#include <stdio.h>
+#include <string.h>
+
+#include "sp2_internal.h"
+
+namespace sp2 {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NUM_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
+constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
+
+// Instruction descriptor, kind::f16: D=F32 (bits 4-5 = 1), A=BF16 (bits 7-9 = 1),
+// B=BF16 (bits 10-12 = 1), both K-major (bits 15,16 = 0), N>>3 at bit 17, M>>4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete. Gives up (returning
+// false) when the abort flag is raised or after TIMEOUT_NS, raising the flag.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag) {
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*((volatile int*)abort_flag)) return false;
+      if (globaltimer() - t0 > TIMEOUT_NS) {
+        atomicExch(abort_flag, 1);
+        return false;
+      }
+    }
+  }
+}
+
+// Same, ignoring the abort flag (drain of copies in flight), with its own limit.
+__device__ void mbar_wait_drain(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > limit_ns) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with
+// 128-byte swizzling: rows of 128 B, 8-row atoms of 1024 B (SBO = 1024),
+// LBO unused for this layout (1), descriptor version 1, layout SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void store_split(float* m, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                            int64_t idx, float v) {
+  m[idx] = v;
+  __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[idx] = h;
+  lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+          const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+          int nkb, int epi, int64_t np, float* __restrict__ out, __nv_bfloat16* __restrict__ out_hi,
+          __nv_bfloat16* __restrict__ out_lo, const float* __restrict__ xprev,
+          double2* __restrict__ part, const Tile* __restrict__ tiles, DevState* st, int step) {
+  {
+    const int m = *((volatile const int*)&st->stop_at);
+    if ((m != 0 && step > m) || *((volatile const int*)&st->abort_flag)) return;
+  }
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  __shared__ double red1[4], red2[4];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Tile t = tiles[blockIdx.x];
+  int* abortf = &st->abort_flag;
+  const int total_kb = 3 * nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA_hi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB_hi)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < total_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abortf)) break;
+        const int seg = kb / nkb;
+        const int kx = (kb - seg * nkb) * BK;
+        const CUtensorMap* ma = seg < 2 ? &mA_hi : &mA_lo;
+        const CUtensorMap* mb = seg == 1 ? &mB_lo : &mB_hi;
+        uint8_t* sa = smem + s * STAGE_BYTES;
+        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_2d(ma, &full[s], sa, kx, t.row0);
+        tma_load_2d(mb, &full[s], sa + A_BYTES, kx, t.col0);
+        issued = kb + 1;
+      }
+      if (issued < total_kb) {
+        // aborted: let the copies already issued land before the CTA exits
+        const int first = issued > STAGES ? issued - STAGES : 0;
+        for (int kb = first; kb < issued; ++kb)
+          mbar_wait_drain(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, 200000000ull);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int kb = 0; kb < total_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph, abortf)) break;
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+        const uint64_t adesc = sdesc_sw128(a_addr);
+        const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          // advance 16 bf16 = 32 bytes along K inside the swizzled row: +2 in 16-byte units
+          umma_bf16(tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                    (kb > 0 || k > 0) ? 1u : 0u);
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(accf);
+    }
+  } else {
+    // epilogue warps 2..5
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const int64_t gi = t.row0 + r;
+    bool ok = mbar_wait(accf, 0, abortf);
+    ok = __all_sync(0xffffffffu, ok);
+    tc_fence_after();
+    double t1 = 0.0, t2 = 0.0;
+    if (ok && !*((volatile int*)abortf)) {
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      const int sg = (epi == EPI_SQUARE) ? st->sigma[step] : 1;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        float val[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) val[j] = __uint_as_float(v[j]);
+        const int64_t gj0 = t.col0 + c0;
+        if (epi == EPI_PLAIN) {
+          float4* dst = reinterpret_cast<float4*>(out + gi * np + gj0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
+          continue;
+        }
+        if (gj0 + 15 < gi) continue;  // whole chunk below the diagonal
+        if (sg < 0) {
+          const float4* xp = reinterpret_cast<const float4*>(xprev + gi * np + gj0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float4 x = xp[j];
+            val[4 * j + 0] = 2.0f * x.x - val[4 * j + 0];
+            val[4 * j + 1] = 2.0f * x.y - val[4 * j + 1];
+            val[4 * j + 2] = 2.0f * x.z - val[4 * j + 2];
+            val[4 * j + 3] = 2.0f * x.w - val[4 * j + 3];
+          }
+        }
+        if (gj0 >= gi) {
+          // whole chunk on or above the diagonal: vector stores
+          float4* dm = reinterpret_cast<float4*>(out + gi * np + gj0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dm[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
+          __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            h[j] = __float2bfloat16_rn(val[j]);
+            l[j] = __float2bfloat16_rn(val[j] - __bfloat162float(h[j]));
+          }
+          uint4* dh = reinterpret_cast<uint4*>(out_hi + gi * np + gj0);
+          uint4* dl = reinterpret_cast<uint4*>(out_lo + gi * np + gj0);
+          dh[0] = reinterpret_cast<const uint4*>(h)[0];
+          dh[1] = reinterpret_cast<const uint4*>(h)[1];
+          dl[0] = reinterpret_cast<const uint4*>(l)[0];
+          dl[1] = reinterpret_cast<const uint4*>(l)[1];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (gj0 + j >= gi) store_split(out, out_hi, out_lo, gi * np + gj0 + j, val[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t gj = gj0 + j;
+          if (gj < gi) continue;
+          const double d = (double)val[j];
+          if (gj == gi) {
+            t1 += d;
+            t2 += d * d;
+          } else {
+            store_split(out, out_hi, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
+            t2 += 2.0 * d * d;
+          }
+        }
+      }
+    }
+    if (epi == EPI_SQUARE) {
+      for (int o = 16; o > 0; o >>= 1) {
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+      }
+      if (lane == 0) {
+        red1[q] = t1;
+        red2[q] = t2;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (epi == EPI_SQUARE && threadIdx.x == 0)
+    part[blockIdx.x] = make_double2(red1[0] + red1[1] + red1[2] + red1[3],
+                                    red2[0] + red2[1] + red2[2] + red2[3]);
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D map over a row-major bf16 plane (rows x np), box = 64 columns x box_rows rows.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)np * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+void tc_tile_shape(int* bm, int* bn) {
+  *bm = BM;
+  *bn = BN;
+}
+
+cudaError_t launch_gemm_tc(int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
+                           const float* x_prev, double2* part, const Tile* tiles, int ntiles,
+                           DevState* st, int step, cudaStream_t s, char* errbuf, size_t errlen) {
+  if (ntiles <= 0) return cudaSuccess;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  // TMA box/stride rules: 16-byte aligned bases, np*2-byte row pitch (np % 256 == 0),
+  // every x coordinate a multiple of 64 elements.
+  if ((reinterpret_cast<uintptr_t>(A.hi) | reinterpret_cast<uintptr_t>(A.lo) |
+       reinterpret_cast<uintptr_t>(B.hi) | reinterpret_cast<uintptr_t>(B.lo)) & 15u ||
+      np % 256 != 0 || A.rows % BM != 0 || B.rows % BN != 0) {
+    snprintf(errbuf, errlen, "tcgen05 product: operand alignment/shape violates the TMA rules");
+    return cudaErrorInvalidValue;
+  }
+  CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
+  if (!make_map(&ma_hi, A.hi, A.rows, np, BM) || !make_map(&ma_lo, A.lo, A.rows, np, BM) ||
+      !make_map(&mb_hi, B.hi, B.rows, np, BN) || !make_map(&mb_lo, B.lo, B.rows, np, BN)) {
+    snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
+    return cudaErrorInvalidValue;
+  }
+  const int nkb = (int)(np / BK);
+  k_gemm_tc<<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
+      ma_hi, ma_lo, mb_hi, mb_lo, nkb, epi, np, static_cast<float*>(out.master), out.hi, out.lo,
+      x_prev, part, tiles, st, step);
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

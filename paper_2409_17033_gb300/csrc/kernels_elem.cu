@@ -1,0 +1,408 @@
+// Element-wise and reduction kernels of the SP2 path: spectral bounds, the
+// initial scaling X_1 = alpha I + beta H, the device-side branch/stop decision,
+// the symmetrised response update, output copies and the response contraction.
+// All reductions accumulate in FP64 in a fixed order (deterministic).
+#include <math.h>
+
+#include "sp2_internal.h"
+
+namespace sp2 {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double ld_as_double(const void* p, int64_t idx) {
+  return (double)(static_cast<const T*>(p)[idx]);
+}
+
+__device__ __forceinline__ double ld_any(const void* p, int64_t idx, int dtype) {
+  return dtype == SP2_F64 ? ld_as_double<double>(p, idx) : ld_as_double<float>(p, idx);
+}
+
+// block-wide sum of a double (blockDim.x multiple of 32, <= 1024)
+__device__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;  // valid in thread 0
+}
+
+// NaN-propagating min / max
+__device__ __forceinline__ double nmin(double a, double b) { return (isnan(a) || isnan(b)) ? NAN : fmin(a, b); }
+__device__ __forceinline__ double nmax(double a, double b) { return (isnan(a) || isnan(b)) ? NAN : fmax(a, b); }
+
+__device__ double2 block_minmax(double lo, double hi) {
+  __shared__ double rlo[32], rhi[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = nmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = nmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { rlo[w] = lo; rhi[w] = hi; }
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  lo = (threadIdx.x < nw) ? rlo[threadIdx.x] : INFINITY;
+  hi = (threadIdx.x < nw) ? rhi[threadIdx.x] : -INFINITY;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = nmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = nmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+  return make_double2(lo, hi);
+}
+
+// ------------------------------------------------------------ Gershgorin
+// Row i contributes H_ii -/+ sum_{j != i} |H_ij| (Sec. II: spectral bound
+// estimates eps_min, eps_max, read as Gershgorin discs).
+__global__ void k_bounds(const void* H, int64_t n, int dtype, double2* part) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    double r = 0.0, d = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      double v = ld_any(H, i * n + j, dtype);
+      if (j == i) d = v; else r += fabs(v);
+    }
+    r = block_sum(r);
+    d = block_sum(d);
+    if (threadIdx.x == 0) { lo = nmin(lo, d - r); hi = nmax(hi, d + r); }
+  }
+  double2 mm = block_minmax(lo, hi);
+  if (threadIdx.x == 0) part[blockIdx.x] = mm;
+}
+
+__global__ void k_bounds_final(const double2* part, int nparts, DevState* st) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    lo = nmin(lo, part[i].x);
+    hi = nmax(hi, part[i].y);
+  }
+  double2 mm = block_minmax(lo, hi);
+  if (threadIdx.x == 0) { st->bounds[0] = mm.x; st->bounds[1] = mm.y; }
+}
+
+// ------------------------------------------------------------ init
+__device__ __forceinline__ void store_elem(MatBuf d, int mode, int64_t idx, double v) {
+  if (mode == SP2_MODE_FP64) {
+    static_cast<double*>(d.master)[idx] = v;
+  } else {
+    float f = (float)v;
+    static_cast<float*>(d.master)[idx] = f;
+    if (mode == SP2_MODE_BF16X2) {
+      __nv_bfloat16 h = __float2bfloat16_rn(f);
+      d.hi[idx] = h;
+      d.lo[idx] = __float2bfloat16_rn(f - __bfloat162float(h));
+    }
+  }
+}
+
+__device__ __forceinline__ double stored_value(int mode, double v) {
+  return mode == SP2_MODE_FP64 ? v : (double)(float)v;
+}
+
+__global__ void k_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
+                       int diag_only, int symmetrize, double alpha, double beta, int mode,
+                       MatBuf dst, double2* part) {
+  double t1 = 0.0, t2 = 0.0;
+  const int64_t rows = batch * np;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int64_t b = r / np, i = r % np;
+    for (int64_t j = threadIdx.x; j < np; j += blockDim.x) {
+      double v = 0.0;
+      if (i < n && j < n) {
+        if (diag_only) {
+          if (i == j) v = beta * ld_any(src, b * n + i, dtype);
+        } else if (symmetrize) {
+          v = beta * (0.5 * (ld_any(src, (b * n + i) * n + j, dtype) +
+                             ld_any(src, (b * n + j) * n + i, dtype)));
+        } else {
+          v = beta * ld_any(src, (b * n + i) * n + j, dtype);
+        }
+        if (i == j) v += alpha;
+      }
+      store_elem(dst, mode, r * np + j, v);
+      double s = stored_value(mode, v);
+      if (i == j) t1 += s;
+      t2 += s * s;
+    }
+  }
+  if (part) {
+    t1 = block_sum(t1);
+    __syncthreads();
+    t2 = block_sum(t2);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(t1, t2);
+  }
+}
+
+// ------------------------------------------------------------ decide
+__global__ void k_decide(const double2* part, DevState* st, DecideParams p) {
+  double t1 = 0.0, t2 = 0.0;
+  for (int i = threadIdx.x; i < p.nparts; i += blockDim.x) {
+    t1 += part[i].x;
+    t2 += part[i].y;
+  }
+  t1 = block_sum(t1);
+  __syncthreads();
+  t2 = block_sum(t2);
+  if (threadIdx.x != 0) return;
+  if (st->stop_at != 0) return;  // already stopped: later steps are no-ops
+  const int n = p.n;
+  st->t1[n] = t1;
+  st->t2[n] = t2;
+  if (!isfinite(t1) || !isfinite(t2)) {
+    st->nonfinite = 1;
+    st->stop_at = (n - 1 >= 1) ? n - 1 : -1;
+    return;
+  }
+  const int s = n - 1;  // the step that produced X_n (0 for X_1)
+  if (p.fixed_m > 0) {
+    if (s == p.fixed_m) st->stop_at = s;
+    return;  // branches preset by the host
+  }
+  if (s >= 1 && s >= p.min_iter) {
+    const double e = fabs(t1 - t2);
+    bool stop = false;
+    if (p.idem_tol > 0.0 && e <= p.idem_tol) stop = true;
+    if (!stop && s >= 2 && p.floor_gate > 0.0) {
+      const double e2 = fabs(st->t1[n - 2] - st->t2[n - 2]);
+      if (e2 <= p.floor_gate && e >= e2) stop = true;
+    }
+    if (stop) {
+      st->stop_at = s;
+      return;
+    }
+  }
+  // Eq. DM0 branch: the trace after X^2 is t2, after 2X - X^2 it is 2 t1 - t2.
+  st->sigma[n] = (fabs(t2 - p.nocc) <= fabs(2.0 * t1 - t2 - p.nocc)) ? 1 : -1;
+}
+
+__device__ __forceinline__ bool halted(const DevState* st, int step) {
+  const int m = *((volatile const int*)&st->stop_at);
+  return m != 0 && step > m;
+}
+
+// ------------------------------------------------------------ symmetrised update
+// Y_{n+1} = (1 - sigma) Y_n + sigma (Z + Z^T), Z = Y_n X_n (Eqs. DM1-DM3: X_n Y_n = (Y_n X_n)^T
+// for symmetric X_n, Y_n). One block per 32x32 tile pair (I <= J); both tiles written.
+template <typename ZT, int MODE>
+__global__ void k_symm_update(const ZT* __restrict__ Z, MatBuf yin, MatBuf yout, int64_t np,
+                              const DevState* st, int step) {
+  if (halted(st, step)) return;
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  const int64_t b = blockIdx.z;
+  const int64_t base = b * np * np;
+  __shared__ ZT zij[32][33];
+  __shared__ ZT zji[32][33];
+  __shared__ ZT yt[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int sg = st->sigma[step];
+  for (int k = 0; k < 32; k += 8) {
+    zij[ty + k][tx] = Z[base + (int64_t)(I * 32 + ty + k) * np + J * 32 + tx];
+    zji[ty + k][tx] = Z[base + (int64_t)(J * 32 + ty + k) * np + I * 32 + tx];
+  }
+  __syncthreads();
+  for (int k = 0; k < 32; k += 8) {
+    const int r = ty + k, c = tx;
+    const int64_t idx = base + (int64_t)(I * 32 + r) * np + J * 32 + c;
+    ZT s = zij[r][c] + zji[c][r];
+    ZT y;
+    if (sg > 0) {
+      y = s;
+    } else {
+      ZT yo = static_cast<const ZT*>(yin.master)[idx];
+      y = (ZT)2 * yo - s;
+    }
+    yt[r][c] = y;
+    static_cast<ZT*>(yout.master)[idx] = y;
+    if (MODE == SP2_MODE_BF16X2) {
+      __nv_bfloat16 h = __float2bfloat16_rn((float)y);
+      yout.hi[idx] = h;
+      yout.lo[idx] = __float2bfloat16_rn((float)y - __bfloat162float(h));
+    }
+  }
+  if (I == J) return;
+  __syncthreads();
+  for (int k = 0; k < 32; k += 8) {
+    const int r = ty + k, c = tx;
+    const int64_t idx = base + (int64_t)(J * 32 + r) * np + I * 32 + c;
+    ZT y = yt[c][r];
+    static_cast<ZT*>(yout.master)[idx] = y;
+    if (MODE == SP2_MODE_BF16X2) {
+      __nv_bfloat16 h = __float2bfloat16_rn((float)y);
+      yout.hi[idx] = h;
+      yout.lo[idx] = __float2bfloat16_rn((float)y - __bfloat162float(h));
+    }
+  }
+}
+
+// ------------------------------------------------------------ output copy
+__global__ void k_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
+                           double scale, void* dst, int dtype) {
+  const int64_t total = batch * n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (n * n), rem = t % (n * n), i = rem / n, j = rem % n;
+    const int64_t s = (b * np + i) * np + j;
+    double v = mode == SP2_MODE_FP64 ? static_cast<const double*>(src.master)[s]
+                                     : (double)static_cast<const float*>(src.master)[s];
+    v *= scale;
+    if (dtype == SP2_F64) static_cast<double*>(dst)[t] = v;
+    else static_cast<float*>(dst)[t] = (float)v;
+  }
+}
+
+__global__ void k_split(MatBuf m, int64_t total) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    float f = static_cast<const float*>(m.master)[t];
+    __nv_bfloat16 h = __float2bfloat16_rn(f);
+    m.hi[t] = h;
+    m.lo[t] = __float2bfloat16_rn(f - __bfloat162float(h));
+  }
+}
+
+// ------------------------------------------------------------ contraction
+// out[l,k] = sum_ij P_l[i,j] Q_k[i,j] (Eqs. expectation, direct, dual), FP64
+// accumulation, per-block partials then a fixed-order second pass.
+template <typename T>
+__global__ void k_contract_dense(const T* __restrict__ P, const T* __restrict__ Q, int64_t K,
+                                 int64_t nn, double* part, int nparts) {
+  const int64_t pair = blockIdx.y;
+  const int64_t l = pair / K, k = pair % K;
+  const T* p = P + l * nn;
+  const T* q = Q + k * nn;
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn;
+       t += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)p[t] * (double)q[t];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[pair * nparts + blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void k_contract_diag(const T* __restrict__ P, const T* __restrict__ Q, int64_t K,
+                                int64_t n, double* part, int nparts) {
+  const int64_t pair = blockIdx.y;
+  const int64_t l = pair / K, k = pair % K;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)P[l * n * n + i * n + i] * (double)Q[k * n + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[pair * nparts + blockIdx.x] = acc;
+}
+
+__global__ void k_contract_final(const double* part, int nparts, double* out) {
+  const int64_t pair = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[pair * nparts + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[pair] = acc;
+}
+
+inline int grid_for(int64_t total, int threads, int cap) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+int bounds_nparts(int64_t n) { return (int)(n < 1024 ? (n < 1 ? 1 : n) : 1024); }
+
+cudaError_t launch_bounds(const void* H, int64_t n, int dtype, double2* part, int nparts,
+                          DevState* st, cudaStream_t s) {
+  k_bounds<<<nparts, kRedThreads, 0, s>>>(H, n, dtype, part);
+  k_bounds_final<<<1, 1024, 0, s>>>(part, nparts, st);
+  return cudaGetLastError();
+}
+
+int init_nparts(int64_t np) { return (int)(np < 1024 ? np : 1024); }
+
+cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
+                        int diag_only, int symmetrize, double alpha, double beta, int mode,
+                        MatBuf dst, double2* part, int nparts, cudaStream_t s) {
+  int grid = part ? nparts : grid_for(batch * np, 1, 4096);
+  k_init<<<grid, kRedThreads, 0, s>>>(src, n, np, batch, dtype, diag_only, symmetrize, alpha,
+                                      beta, mode, dst, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide(const double2* part, DevState* st, DecideParams p, cudaStream_t s) {
+  k_decide<<<1, kRedThreads, 0, s>>>(part, st, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t np, int64_t batch,
+                               int mode, const DevState* st, int step, cudaStream_t s) {
+  dim3 grid((unsigned)(np / 32), (unsigned)(np / 32), (unsigned)batch), block(32, 8);
+  if (mode == SP2_MODE_FP64)
+    k_symm_update<double, SP2_MODE_FP64><<<grid, block, 0, s>>>(static_cast<const double*>(Z), y_in,
+                                                                y_out, np, st, step);
+  else if (mode == SP2_MODE_FP32)
+    k_symm_update<float, SP2_MODE_FP32><<<grid, block, 0, s>>>(static_cast<const float*>(Z), y_in,
+                                                               y_out, np, st, step);
+  else
+    k_symm_update<float, SP2_MODE_BF16X2><<<grid, block, 0, s>>>(static_cast<const float*>(Z), y_in,
+                                                                 y_out, np, st, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
+                            double scale, void* dst, int dtype, cudaStream_t s) {
+  k_copy_out<<<grid_for(batch * n * n, 256, 8192), 256, 0, s>>>(src, n, np, batch, mode, scale,
+                                                                 dst, dtype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, cudaStream_t s) {
+  k_split<<<grid_for(rows * np, 256, 8192), 256, 0, s>>>(m, rows * np);
+  return cudaGetLastError();
+}
+
+int contract_nparts(int64_t n, int q_diag) {
+  int64_t work = q_diag ? n : n * n;
+  int64_t g = (work + 256 * 16 - 1) / (256 * 16);
+  if (g < 1) g = 1;
+  if (g > 304) g = 304;
+  return (int)g;
+}
+
+cudaError_t launch_contract(const void* P, int64_t L, const void* Q, int64_t K, int64_t n,
+                            int dtype, int q_diag, double* part, int nparts, double* out,
+                            cudaStream_t s) {
+  dim3 grid((unsigned)nparts, (unsigned)(L * K));
+  if (dtype == SP2_F64) {
+    if (q_diag)
+      k_contract_diag<double><<<grid, 256, 0, s>>>(static_cast<const double*>(P),
+                                                   static_cast<const double*>(Q), K, n, part, nparts);
+    else
+      k_contract_dense<double><<<grid, 256, 0, s>>>(static_cast<const double*>(P),
+                                                    static_cast<const double*>(Q), K, n * n, part,
+                                                    nparts);
+  } else {
+    if (q_diag)
+      k_contract_diag<float><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
+                                                  static_cast<const float*>(Q), K, n, part, nparts);
+    else
+      k_contract_dense<float><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
+                                                   static_cast<const float*>(Q), K, n * n, part,
+                                                   nparts);
+  }
+  k_contract_final<<<(unsigned)(L * K), 256, 0, s>>>(part, nparts, out);
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

@@ -1,0 +1,911 @@
+// C ABI of libsp2.so (declared in include/sp2.h) and the host-side drivers of
+// the SP2 recursions. The host only sequences kernels on the handle's stream;
+// every arithmetic step (bounds, scaling, products, branch choice, stopping
+// test, response updates, contractions) runs on the device.
+#include <stdarg.h>
+#include <cmath>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sp2_internal.h"
+
+using namespace sp2;
+
+struct sp2_handle_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t limit = 0;
+  size_t held = 0;
+  std::string err;
+  struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  std::map<std::string, Buf> bufs;
+  struct TileList {
+    Tile* d = nullptr;
+    int n = 0;
+  };
+  std::map<std::string, TileList> tiles;
+  DevState* d_state = nullptr;
+  DevState* h_state = nullptr;  // pinned mirror
+  std::vector<cudaEvent_t> events;  // pool for time_kernels (start/stop pairs)
+
+  // X_n history kept for sp2_adjoint
+  struct History {
+    bool valid = false;
+    int64_t n = 0, np = 0;
+    int mode = 0, M = 0, k = 4;
+    double beta = 0.0;
+    std::vector<int> sigma;  // sigma[1..M]
+  } hist;
+};
+
+namespace {
+
+int fail(sp2_handle_t h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+#define CK(expr)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, SP2_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int r_ = (expr);         \
+    if (r_ != SP2_OK) return r_; \
+  } while (0)
+
+// --------------------------------------------------------------- workspace
+int ws(sp2_handle_t h, const std::string& name, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 256;
+  auto& b = h->bufs[name];
+  if (b.bytes >= bytes) {
+    *out = b.p;
+    return SP2_OK;
+  }
+  if (b.p) {
+    cudaFree(b.p);
+    h->held -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (h->limit && h->held + bytes > h->limit)
+    return fail(h, SP2_ENOMEM, "workspace limit %zu bytes exceeded (need %zu more for %s)",
+                h->limit, bytes, name.c_str());
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SP2_ENOMEM, "cudaMalloc(%zu) for %s failed: %s", bytes, name.c_str(),
+                cudaGetErrorString(e));
+  }
+  b.p = p;
+  b.bytes = bytes;
+  h->held += bytes;
+  *out = p;
+  return SP2_OK;
+}
+
+void ws_free(sp2_handle_t h, const std::string& name) {
+  auto it = h->bufs.find(name);
+  if (it == h->bufs.end()) return;
+  if (it->second.p) {
+    cudaFree(it->second.p);
+    h->held -= it->second.bytes;
+  }
+  h->bufs.erase(it);
+}
+
+size_t master_size(int mode) { return mode == SP2_MODE_FP64 ? 8 : 4; }
+
+int mat(sp2_handle_t h, const std::string& name, int64_t rows, int64_t np, int mode, MatBuf* m) {
+  const size_t cnt = (size_t)rows * (size_t)np;
+  *m = MatBuf{};
+  TRY(ws(h, name + ".m", cnt * master_size(mode), &m->master));
+  if (mode == SP2_MODE_BF16X2) {
+    void* p;
+    TRY(ws(h, name + ".h", cnt * 2, &p));
+    m->hi = static_cast<__nv_bfloat16*>(p);
+    TRY(ws(h, name + ".l", cnt * 2, &p));
+    m->lo = static_cast<__nv_bfloat16*>(p);
+  }
+  return SP2_OK;
+}
+
+// --------------------------------------------------------------- host/device staging
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int stage_in(sp2_handle_t h, const std::string& name, const void* p, size_t bytes,
+             const void** dev) {
+  if (bytes == 0 || is_device_ptr(p)) {
+    *dev = p;
+    return SP2_OK;
+  }
+  void* d;
+  TRY(ws(h, "stage." + name, bytes, &d));
+  CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, h->stream));
+  *dev = d;
+  return SP2_OK;
+}
+
+struct OutStage {
+  void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+
+int stage_out(sp2_handle_t h, const std::string& name, void* p, size_t bytes, OutStage* o) {
+  o->user = p;
+  o->bytes = bytes;
+  o->host = !(bytes == 0 || is_device_ptr(p));
+  if (!o->host) {
+    o->dev = p;
+    return SP2_OK;
+  }
+  return ws(h, "stage." + name, bytes, &o->dev);
+}
+
+int finish_out(sp2_handle_t h, const OutStage& o) {
+  if (o.host) CK(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, h->stream));
+  return SP2_OK;
+}
+
+size_t dsize(int dtype) { return dtype == SP2_F64 ? 8 : 4; }
+
+// --------------------------------------------------------------- tile lists
+void tile_shape(int mode, int* bm, int* bn) {
+  if (mode == SP2_MODE_BF16X2) tc_tile_shape(bm, bn);
+  else simt_tile_shape(mode, bm, bn);
+}
+
+// Output tiles of a (rows x np) product in an L2-friendly order: groups of 8
+// row blocks sweep the column blocks together, so CTAs resident at the same
+// time share their operand slices. upper=true keeps only tiles that meet the
+// upper triangle (row0 <= last column), which suffices for symmetric results.
+int tile_list(sp2_handle_t h, int mode, int64_t rows, int64_t np, bool upper, const Tile** d,
+              int* n) {
+  int bm, bn;
+  tile_shape(mode, &bm, &bn);
+  char key[96];
+  snprintf(key, sizeof key, "%d/%lld/%lld/%d", mode, (long long)rows, (long long)np, (int)upper);
+  auto it = h->tiles.find(key);
+  if (it != h->tiles.end()) {
+    *d = it->second.d;
+    *n = it->second.n;
+    return SP2_OK;
+  }
+  std::vector<Tile> v;
+  const int64_t nm = rows / bm, nn = np / bn;
+  const int64_t G = 8;
+  for (int64_t g0 = 0; g0 < nm; g0 += G) {
+    const int64_t gs = (nm - g0) < G ? (nm - g0) : G;
+    for (int64_t cn = 0; cn < nn; ++cn)
+      for (int64_t m = g0; m < g0 + gs; ++m) {
+        const int64_t r0 = m * bm, c0 = cn * bn;
+        if (upper && r0 > c0 + bn - 1) continue;
+        v.push_back(Tile{(int)r0, (int)c0});
+      }
+  }
+  Tile* dp = nullptr;
+  CK(cudaMalloc(&dp, v.size() * sizeof(Tile) + 16));
+  CK(cudaMemcpy(dp, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  h->tiles[key] = sp2_handle_s::TileList{dp, (int)v.size()};
+  *d = dp;
+  *n = (int)v.size();
+  return SP2_OK;
+}
+
+// --------------------------------------------------------------- products
+struct Ctx {
+  sp2_handle_t h;
+  int mode;
+  int64_t n;      // caller's matrix size
+  int64_t np;     // padded size
+  DevState* st;
+  double2* part;  // trace partials (>= max tiles)
+  int64_t launches = 0;   // product launches that did work
+  double flops = 0.0;     // executed product flops
+  double alg = 0.0;       // algorithmic product flops
+  int64_t kernels = 0;    // every kernel launched
+  bool timing = false;
+  std::vector<std::pair<int, int>> timed;  // (step, event-pair index) per timed product launch
+};
+
+int ev_pair(Ctx& c, cudaEvent_t* a, cudaEvent_t* b) {
+  sp2_handle_t h = c.h;
+  const size_t i = c.timed.size();
+  while (h->events.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->events.push_back(e);
+  }
+  *a = h->events[2 * i];
+  *b = h->events[2 * i + 1];
+  return SP2_OK;
+}
+
+// summed duration of the timed product launches of steps <= m
+double timed_ms(Ctx& c, int m) {
+  double tot = 0.0;
+  for (size_t i = 0; i < c.timed.size(); ++i) {
+    if (c.timed[i].first > m) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c.h->events[2 * i], c.h->events[2 * i + 1]) == cudaSuccess)
+      tot += ms;
+    else
+      cudaGetLastError();
+  }
+  return tot;
+}
+
+int64_t timed_count(const Ctx& c, int m) {
+  int64_t k = 0;
+  for (auto& t : c.timed) k += t.first <= m ? 1 : 0;
+  return k;
+}
+
+double k_mult(int mode) { return mode == SP2_MODE_BF16X2 ? 3.0 : 1.0; }
+
+// X_{n+1} = sigma_n>0 ? X_n^2 : 2 X_n - X_n^2, with trace partials; returns #partials
+int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* nparts) {
+  sp2_handle_t h = c.h;
+  const Tile* tl;
+  int nt;
+  TRY(tile_list(h, c.mode, c.np, c.np, true, &tl, &nt));
+  int bm, bn;
+  tile_shape(c.mode, &bm, &bn);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.timing) {
+    TRY(ev_pair(c, &e0, &e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  if (c.mode == SP2_MODE_BF16X2) {
+    char eb[256] = {0};
+    TcOperand a{xin.hi, xin.lo, c.np};
+    cudaError_t e = launch_gemm_tc(EPI_SQUARE, a, a, c.np, xout, static_cast<const float*>(xin.master),
+                                   c.part, tl, nt, c.st, step, h->stream, eb, sizeof eb);
+    if (e != cudaSuccess) return fail(h, SP2_ECUDA, "square product: %s %s", cudaGetErrorString(e), eb);
+  } else {
+    CK(launch_gemm_simt(c.mode, EPI_SQUARE, xin.master, c.np, xin.master, c.np, xout.master,
+                        xin.master, c.part, tl, nt, c.st, step, h->stream));
+  }
+  if (c.timing) {
+    CK(cudaEventRecord(e1, h->stream));
+    c.timed.push_back({step, 0});
+  }
+  c.launches++;
+  c.kernels++;
+  c.flops += 2.0 * bm * bn * (double)c.np * k_mult(c.mode) * nt;
+  c.alg += (double)c.n * (double)(c.n + 1) * (double)c.n * k_mult(c.mode);
+  *nparts = nt;
+  return SP2_OK;
+}
+
+// Y_{n+1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n) for a batch of Y
+int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout, int64_t batch,
+                  int step) {
+  sp2_handle_t h = c.h;
+  const int64_t rows = batch * c.np;
+  void* z;
+  TRY(ws(h, "Z", (size_t)rows * c.np * master_size(c.mode), &z));
+  const Tile* tl;
+  int nt;
+  TRY(tile_list(h, c.mode, rows, c.np, false, &tl, &nt));
+  int bm, bn;
+  tile_shape(c.mode, &bm, &bn);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.timing) {
+    TRY(ev_pair(c, &e0, &e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  if (c.mode == SP2_MODE_BF16X2) {
+    char eb[256] = {0};
+    TcOperand a{yin.hi, yin.lo, rows}, b{x.hi, x.lo, c.np};
+    MatBuf zo;
+    zo.master = z;
+    cudaError_t e = launch_gemm_tc(EPI_PLAIN, a, b, c.np, zo, nullptr, c.part, tl, nt, c.st, step,
+                                   h->stream, eb, sizeof eb);
+    if (e != cudaSuccess) return fail(h, SP2_ECUDA, "response product: %s %s", cudaGetErrorString(e), eb);
+  } else {
+    CK(launch_gemm_simt(c.mode, EPI_PLAIN, yin.master, rows, x.master, c.np, z, nullptr, c.part,
+                        tl, nt, c.st, step, h->stream));
+  }
+  if (c.timing) {
+    CK(cudaEventRecord(e1, h->stream));
+    c.timed.push_back({step, 0});
+  }
+  CK(launch_symm_update(z, yin, yout, c.np, batch, c.mode, c.st, step, h->stream));
+  c.launches++;
+  c.kernels += 2;
+  c.flops += 2.0 * bm * bn * (double)c.np * k_mult(c.mode) * nt;
+  c.alg += 2.0 * (double)batch * (double)c.n * (double)c.n * (double)c.n * k_mult(c.mode);
+  return SP2_OK;
+}
+
+int validate_opts(sp2_handle_t h, const sp2_opts* o) {
+  if (o->mode != SP2_MODE_FP64 && o->mode != SP2_MODE_FP32 && o->mode != SP2_MODE_BF16X2)
+    return fail(h, SP2_EINVAL, "unknown mode %d", o->mode);
+  if (o->max_iter < 1 || o->max_iter > SP2_MAX_ITER)
+    return fail(h, SP2_EINVAL, "max_iter %d outside 1..%d", o->max_iter, SP2_MAX_ITER);
+  if (o->fixed_m > SP2_MAX_ITER) return fail(h, SP2_EINVAL, "fixed_m > %d", SP2_MAX_ITER);
+  if (o->fixed_m > 0 && !o->sigma_in) return fail(h, SP2_EINVAL, "fixed_m without sigma_in");
+  if (o->fixed_m > 0)
+    for (int i = 0; i < o->fixed_m; ++i)
+      if (o->sigma_in[i] != 1 && o->sigma_in[i] != -1)
+        return fail(h, SP2_EINVAL, "sigma_in[%d] = %d is not +-1", i, (int)o->sigma_in[i]);
+  if (o->ckpt_k < 1) return fail(h, SP2_EINVAL, "ckpt_k must be >= 1");
+  return SP2_OK;
+}
+
+sp2_opts resolve(const sp2_opts* in) {
+  sp2_opts o;
+  sp2_default_opts(&o);
+  if (in) o = *in;
+  if (o.max_iter == 0) o.max_iter = 100;
+  if (o.min_iter < 0) o.min_iter = 4;
+  if (o.floor_gate < 0) o.floor_gate = 0.1;
+  if (o.ckpt_k == 0) o.ckpt_k = 4;
+  return o;
+}
+
+int check_common(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc) {
+  if (!h) return SP2_EINVAL;
+  if (N < 0) return fail(h, SP2_EINVAL, "N = %lld < 0", (long long)N);
+  if (N > (int64_t)1 << 20) return fail(h, SP2_EINVAL, "N = %lld too large", (long long)N);
+  if (dtype != SP2_F64 && dtype != SP2_F32) return fail(h, SP2_EINVAL, "unknown dtype %d", dtype);
+  if (N > 0 && !H) return fail(h, SP2_EINVAL, "H is NULL");
+  if (!(nocc >= 0.0 && nocc <= (double)N)) return fail(h, SP2_EINVAL, "nocc %g outside [0, N]", nocc);
+  return SP2_OK;
+}
+
+int poll_state(sp2_handle_t h) {
+  CK(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->h_state->abort_flag)
+    return fail(h, SP2_ETIMEOUT, "a device-side wait timed out in a product kernel");
+  return SP2_OK;
+}
+
+// --------------------------------------------------------------- the SP2 driver
+struct Sp2Out {
+  int M = 0;
+  bool converged = false;
+  double alpha = 0, beta = 0, emin = 0, emax = 0;
+  int xslot = 0;  // buffer holding X_{M+1}
+  int yslot = 0;  // buffer holding Y_{M+1}
+};
+
+// Runs Eq. DM0 on the padded X_1 = alpha I + beta H. If ybatch > 0, the
+// response Y of Eq. DMPert / DMSuscept is carried along (merged form,
+// Appendix), starting from Y_1 = beta B. If keep, X_n is checkpointed every
+// ckpt_k steps for the adjoint.
+int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, const sp2_opts& o,
+            const void* Bd, int64_t ybatch, int b_diag, bool keep, MatBuf X[2], MatBuf Y[2],
+            Ctx& c, Sp2Out* out) {
+  const int64_t np = pad_n(n);
+  const int mode = o.mode;
+  // spectral bounds (Sec. II)
+  double emin = o.eps_min, emax = o.eps_max;
+  CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));
+  if (!(emin < emax)) {
+    const int nb = bounds_nparts(n);
+    void* bp;
+    TRY(ws(h, "bounds.part", nb * sizeof(double2), &bp));
+    CK(launch_bounds(Hd, n, dtype, static_cast<double2*>(bp), nb, h->d_state, h->stream));
+    c.kernels += 2;
+    TRY(poll_state(h));
+    emin = h->h_state->bounds[0];
+    emax = h->h_state->bounds[1];
+    if (!std::isfinite(emin) || !std::isfinite(emax))
+      return fail(h, SP2_ENONFINITE, "non-finite spectral bounds (NaN/Inf in H)");
+  }
+  if (!(emax > emin)) {  // point spectrum: any interval around it maps into [0, 1]
+    emin -= 0.5;
+    emax += 0.5;
+  }
+  const double w = emax - emin;
+  const double alpha = emax / w, beta = -1.0 / w;
+  out->alpha = alpha;
+  out->beta = beta;
+  out->emin = emin;
+  out->emax = emax;
+
+  if (o.fixed_m > 0) {
+    for (int i = 0; i < o.fixed_m; ++i) h->h_state->sigma[i + 1] = o.sigma_in[i];
+    CK(cudaMemcpyAsync(h->d_state->sigma, h->h_state->sigma, sizeof(int) * (o.fixed_m + 2),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // h_state is reused by later polls
+  }
+
+  TRY(mat(h, "X0", np, np, mode, &X[0]));
+  TRY(mat(h, "X1", np, np, mode, &X[1]));
+  const int ni = init_nparts(np);
+  CK(launch_init(Hd, n, np, 1, dtype, 0, 0, alpha, beta, mode, X[1], c.part, ni, h->stream));
+  c.kernels++;
+  DecideParams dp;
+  dp.nocc = nocc;
+  dp.idem_tol = o.idem_tol;
+  dp.floor_gate = o.floor_gate;
+  dp.min_iter = o.min_iter;
+  dp.max_iter = o.max_iter;
+  dp.fixed_m = o.fixed_m;
+  dp.n = 1;
+  dp.nparts = ni;
+  CK(launch_decide(c.part, c.st, dp, h->stream));
+  c.kernels++;
+  if (ybatch > 0) {
+    TRY(mat(h, "Y0", ybatch * np, np, mode, &Y[0]));
+    TRY(mat(h, "Y1", ybatch * np, np, mode, &Y[1]));
+    CK(launch_init(Bd, n, np, ybatch, dtype, b_diag, 0, 0.0, beta, mode, Y[1], nullptr, 0, h->stream));
+    c.kernels++;
+  }
+
+  const int maxit = o.fixed_m > 0 ? o.fixed_m : o.max_iter;
+  const int chunk = np <= 1024 ? 8 : (np <= 4096 ? 2 : 1);
+  const size_t xbytes = (size_t)np * np * master_size(mode);
+  int M = 0;
+  bool stopped = false;
+  const double f0 = c.flops, a0 = c.alg;
+  const int64_t l0 = c.launches;
+  double fstep = 0.0, astep = 0.0;
+  int64_t lstep = 0;
+  for (int step = 1; step <= maxit && !stopped; ++step) {
+    const MatBuf& xin = X[step % 2];
+    const MatBuf& xo = X[(step + 1) % 2];
+    if (keep && (step - 1) % o.ckpt_k == 0) {
+      void* ck;
+      TRY(ws(h, "ckpt." + std::to_string((step - 1) / o.ckpt_k), xbytes, &ck));
+      CK(cudaMemcpyAsync(ck, xin.master, xbytes, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (ybatch > 0) TRY(response_step(c, xin, Y[step % 2], Y[(step + 1) % 2], ybatch, step));
+    int nparts = 0;
+    TRY(square_step(c, xin, xo, step, &nparts));
+    dp.n = step + 1;
+    dp.nparts = nparts;
+    CK(launch_decide(c.part, c.st, dp, h->stream));
+    c.kernels++;
+    if (step == 1) {
+      fstep = c.flops - f0;
+      astep = c.alg - a0;
+      lstep = c.launches - l0;
+    }
+    if (step % chunk == 0 || step == maxit) {
+      TRY(poll_state(h));
+      const DevState& s = *h->h_state;
+      if (s.nonfinite) return fail(h, SP2_ENONFINITE, "non-finite trace at step %d", step);
+      if (s.stop_at != 0) {
+        M = s.stop_at;
+        stopped = true;
+      }
+    }
+  }
+  if (!stopped) M = maxit;
+  out->M = M;
+  out->converged = stopped;
+  out->xslot = (M + 1) % 2;
+  out->yslot = (M + 1) % 2;
+  // executed-work accounting covers only the steps that ran (later launches were no-ops)
+  c.flops = f0 + fstep * M;
+  c.alg = a0 + astep * M;
+  c.launches = l0 + lstep * M;
+  return SP2_OK;
+}
+
+void fill_info(sp2_handle_t h, const Sp2Out& r, const Ctx& c, sp2_info* info) {
+  if (!info) return;
+  memset(info, 0, sizeof *info);
+  info->M = r.M;
+  info->converged = r.converged ? 1 : 0;
+  info->alpha = r.alpha;
+  info->beta = r.beta;
+  info->eps_min = r.emin;
+  info->eps_max = r.emax;
+  const DevState& s = *h->h_state;
+  for (int i = 1; i <= r.M; ++i) info->sigma[i - 1] = (int8_t)s.sigma[i];
+  for (int i = 1; i <= r.M + 1; ++i) info->errors[i - 1] = s.t1[i] - s.t2[i];
+  info->trace = s.t1[r.M + 1];
+  info->idem_err = s.t1[r.M + 1] - s.t2[r.M + 1];
+  info->n_gemm_launches = c.launches;
+  info->executed_flops = c.flops;
+  info->algorithmic_flops = c.alg;
+  info->kernel_launches = c.kernels;
+}
+
+// timing fields; call after the stream has been synchronised
+void fill_timing(Ctx& c, int m, sp2_info* info) {
+  if (!info) return;
+  info->n_gemm_launches = c.launches;
+  info->executed_flops = c.flops;
+  info->algorithmic_flops = c.alg;
+  info->kernel_launches = c.kernels;
+  if (c.timing) {
+    info->product_ms = timed_ms(c, m);
+    info->product_launches_timed = timed_count(c, m);
+  }
+}
+
+int make_ctx(sp2_handle_t h, int mode, int64_t n, int64_t np, bool timing, Ctx* c) {
+  c->h = h;
+  c->mode = mode;
+  c->n = n;
+  c->np = np;
+  c->timing = timing;
+  c->st = h->d_state;
+  int bm, bn;
+  tile_shape(mode, &bm, &bn);
+  int64_t maxp = (np / bm) * (np / bn) + 8;
+  if (maxp < init_nparts(np)) maxp = init_nparts(np);
+  void* p;
+  TRY(ws(h, "part", (size_t)maxp * sizeof(double2), &p));
+  c->part = static_cast<double2*>(p);
+  return SP2_OK;
+}
+
+// Eq. DM2 over the kept history: G_{M+1} = B, G_n = (1 - s_n) G_{n+1} + s_n (G_{n+1} X_n + X_n G_{n+1}),
+// n = M..1; result beta * G_1. X_n is restored from the checkpoint of its
+// segment and the segment is recomputed forward with the stored branches.
+int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int symmetrize,
+                int dtype, void* outd, int out_dtype, Ctx& c) {
+  auto& hs = h->hist;
+  const int64_t np = hs.np, n = hs.n;
+  const int mode = hs.mode, M = hs.M, k = hs.k;
+  // branch signs for the step kernels; no stop
+  void* stp;
+  TRY(ws(h, "adj.state", sizeof(DevState), &stp));
+  DevState* ast = static_cast<DevState*>(stp);
+  memset(h->h_state, 0, sizeof(DevState));
+  for (int i = 1; i <= M; ++i) h->h_state->sigma[i] = hs.sigma[i];
+  CK(cudaMemcpyAsync(ast, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  c.st = ast;
+
+  MatBuf G[2];
+  TRY(mat(h, "G0", batch * np, np, mode, &G[0]));
+  TRY(mat(h, "G1", batch * np, np, mode, &G[1]));
+  int gs = (M + 1) % 2;  // slot of G_{M+1}
+  CK(launch_init(Bd, n, np, batch, dtype, b_diag, symmetrize, 0.0, 1.0, mode, G[gs], nullptr, 0,
+                 h->stream));
+  c.kernels++;
+  std::vector<MatBuf> seg(k);
+  for (int i = 0; i < k; ++i) TRY(mat(h, "seg." + std::to_string(i), np, np, mode, &seg[i]));
+  const size_t xbytes = (size_t)np * np * master_size(mode);
+  const int nseg = (M + k - 1) / k;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int s0 = j * k + 1;
+    const int s1 = (j * k + k) < M ? (j * k + k) : M;
+    void* ck;
+    TRY(ws(h, "ckpt." + std::to_string(j), xbytes, &ck));
+    CK(cudaMemcpyAsync(seg[0].master, ck, xbytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (mode == SP2_MODE_BF16X2) {
+      CK(launch_split(seg[0], np, np, h->stream));
+      c.kernels++;
+    }
+    for (int s = s0; s < s1; ++s) {
+      int nparts;
+      TRY(square_step(c, seg[s - s0], seg[s - s0 + 1], s, &nparts));
+    }
+    for (int s = s1; s >= s0; --s) {
+      TRY(response_step(c, seg[s - s0], G[gs], G[1 - gs], batch, s));
+      gs = 1 - gs;
+    }
+  }
+  // gs now holds G_1
+  CK(launch_copy_out(G[gs], n, np, batch, mode, hs.beta, outd, out_dtype, h->stream));
+  c.kernels++;
+  c.st = h->d_state;
+  return SP2_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void sp2_default_opts(sp2_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->mode = SP2_MODE_FP32;
+  o->idem_tol = 0.0;
+  o->floor_gate = 0.1;
+  o->max_iter = 100;
+  o->min_iter = 4;
+  o->fixed_m = 0;
+  o->sigma_in = nullptr;
+  o->eps_min = 0.0;
+  o->eps_max = 0.0;
+  o->ckpt_k = 4;
+  o->keep_history = 0;
+}
+
+int sp2_create(sp2_handle_t* out, void* stream, size_t limit) {
+  if (!out) return SP2_EINVAL;
+  *out = nullptr;
+  sp2_handle_t h = new sp2_handle_s();
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->limit = limit;
+  int code = SP2_OK;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaMalloc(&h->d_state, sizeof(DevState)) != cudaSuccess ||
+      cudaMallocHost(&h->h_state, sizeof(DevState)) != cudaSuccess) {
+    cudaGetLastError();
+    code = SP2_ECUDA;
+  }
+  if (code != SP2_OK) {
+    if (h->d_state) cudaFree(h->d_state);
+    delete h;
+    return code;
+  }
+  memset(h->h_state, 0, sizeof(DevState));
+  *out = h;
+  return SP2_OK;
+}
+
+int sp2_destroy(sp2_handle_t h) {
+  if (!h) return SP2_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  for (auto& kv : h->tiles) cudaFree(kv.second.d);
+  if (h->d_state) cudaFree(h->d_state);
+  if (h->h_state) cudaFreeHost(h->h_state);
+  delete h;
+  return SP2_OK;
+}
+
+int sp2_set_stream(sp2_handle_t h, void* stream) {
+  if (!h) return SP2_EINVAL;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return SP2_OK;
+}
+
+const char* sp2_last_error(sp2_handle_t h) { return h ? h->err.c_str() : "null handle"; }
+
+size_t sp2_workspace_bytes(sp2_handle_t h) { return h ? h->held : 0; }
+
+int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc,
+                const sp2_opts* opts_in, void* D, sp2_info* info) {
+  TRY(check_common(h, H, N, dtype, nocc));
+  if (N > 0 && !D) return fail(h, SP2_EINVAL, "D is NULL");
+  sp2_opts o = resolve(opts_in);
+  TRY(validate_opts(h, &o));
+  if (info) memset(info, 0, sizeof *info);
+  if (N == 0) {
+    if (info) info->converged = 1;
+    return SP2_OK;
+  }
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const void* Hd;
+  TRY(stage_in(h, "H", H, mb, &Hd));
+  OutStage od;
+  TRY(stage_out(h, "D", D, mb, &od));
+  const int64_t np = pad_n(N);
+  Ctx c;
+  TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
+  MatBuf X[2], Y[2];
+  Sp2Out r;
+  const bool keep = o.keep_history != 0;
+  if (keep) h->hist.valid = false;
+  TRY(run_sp2(h, Hd, N, dtype, nocc, o, nullptr, 0, 0, keep, X, Y, c, &r));
+  CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
+  c.kernels++;
+  TRY(finish_out(h, od));
+  CK(cudaStreamSynchronize(h->stream));
+  fill_info(h, r, c, info);
+  fill_timing(c, r.M, info);
+  if (keep) {
+    auto& hs = h->hist;
+    hs.valid = true;
+    hs.n = N;
+    hs.np = np;
+    hs.mode = o.mode;
+    hs.M = r.M;
+    hs.k = o.ckpt_k;
+    hs.beta = r.beta;
+    hs.sigma.assign(r.M + 1, 0);
+    for (int i = 1; i <= r.M; ++i) hs.sigma[i] = h->h_state->sigma[i];
+  }
+  if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
+  return SP2_OK;
+}
+
+int sp2_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc, const void* H1,
+                 int64_t K, int h1_diag_only, const sp2_opts* opts_in, void* D, void* D1,
+                 sp2_info* info) {
+  TRY(check_common(h, H, N, dtype, nocc));
+  if (K < 0) return fail(h, SP2_EINVAL, "K < 0");
+  if (N > 0 && K > 0 && (!H1 || !D1)) return fail(h, SP2_EINVAL, "H1 or D1 is NULL");
+  sp2_opts o = resolve(opts_in);
+  TRY(validate_opts(h, &o));
+  if (info) memset(info, 0, sizeof *info);
+  if (N == 0) {
+    if (info) info->converged = 1;
+    return SP2_OK;
+  }
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const size_t b_bytes = (size_t)K * (h1_diag_only ? N : N * N) * dsize(dtype);
+  const void *Hd, *Bd = nullptr;
+  TRY(stage_in(h, "H", H, mb, &Hd));
+  if (K > 0) TRY(stage_in(h, "B", H1, b_bytes, &Bd));
+  OutStage od, oy;
+  if (D) TRY(stage_out(h, "D", D, mb, &od));
+  if (K > 0) TRY(stage_out(h, "Y", D1, (size_t)K * mb, &oy));
+  const int64_t np = pad_n(N);
+  Ctx c;
+  TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
+  MatBuf X[2], Y[2];
+  Sp2Out r;
+  TRY(run_sp2(h, Hd, N, dtype, nocc, o, Bd, K, h1_diag_only, false, X, Y, c, &r));
+  if (D) {
+    CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
+    c.kernels++;
+    TRY(finish_out(h, od));
+  }
+  if (K > 0) {
+    CK(launch_copy_out(Y[r.yslot], N, np, K, o.mode, 1.0, oy.dev, dtype, h->stream));
+    c.kernels++;
+    TRY(finish_out(h, oy));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  fill_info(h, r, c, info);
+  fill_timing(c, r.M, info);
+  if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
+  return SP2_OK;
+}
+
+int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad, sp2_info* info);
+
+int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc,
+                       const void* A, int64_t L, int a_diag_only, int direction,
+                       const sp2_opts* opts_in, void* D, void* chi, sp2_info* info) {
+  TRY(check_common(h, H, N, dtype, nocc));
+  if (L < 0) return fail(h, SP2_EINVAL, "L < 0");
+  if (direction != 0 && direction != 1) return fail(h, SP2_EINVAL, "direction must be 0 or 1");
+  if (N > 0 && L > 0 && (!A || !chi)) return fail(h, SP2_EINVAL, "A or chi is NULL");
+  sp2_opts o = resolve(opts_in);
+  TRY(validate_opts(h, &o));
+  if (direction == 0)
+    return sp2_response(h, H, N, dtype, nocc, A, L, a_diag_only, &o, D, chi, info);
+  if (info) memset(info, 0, sizeof *info);
+  if (N == 0) {
+    if (info) info->converged = 1;
+    return SP2_OK;
+  }
+  // backward: forward pass with checkpoints, then Eq. DM2
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const size_t b_bytes = (size_t)L * (a_diag_only ? N : N * N) * dsize(dtype);
+  const void *Hd, *Bd = nullptr;
+  TRY(stage_in(h, "H", H, mb, &Hd));
+  if (L > 0) TRY(stage_in(h, "B", A, b_bytes, &Bd));
+  OutStage od, oy;
+  if (D) TRY(stage_out(h, "D", D, mb, &od));
+  if (L > 0) TRY(stage_out(h, "Y", chi, (size_t)L * mb, &oy));
+  const int64_t np = pad_n(N);
+  Ctx c;
+  TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
+  MatBuf X[2], Y[2];
+  Sp2Out r;
+  h->hist.valid = false;
+  TRY(run_sp2(h, Hd, N, dtype, nocc, o, nullptr, 0, 0, true, X, Y, c, &r));
+  if (D) {
+    CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
+    c.kernels++;
+    TRY(finish_out(h, od));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  fill_info(h, r, c, info);
+  auto& hs = h->hist;
+  hs.valid = true;
+  hs.n = N;
+  hs.np = np;
+  hs.mode = o.mode;
+  hs.M = r.M;
+  hs.k = o.ckpt_k;
+  hs.beta = r.beta;
+  hs.sigma.assign(r.M + 1, 0);
+  for (int i = 1; i <= r.M; ++i) hs.sigma[i] = h->h_state->sigma[i];
+  if (L > 0) {
+    TRY(run_adjoint(h, Bd, L, a_diag_only, 0, dtype, oy.dev, dtype, c));
+    TRY(finish_out(h, oy));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  fill_timing(c, r.M, info);
+  if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
+  return SP2_OK;
+}
+
+int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad, sp2_info* info) {
+  if (!h) return SP2_EINVAL;
+  if (!h->hist.valid) return fail(h, SP2_ENOSTATE, "no X_n history kept on this handle");
+  if (N != h->hist.n) return fail(h, SP2_ENOSTATE, "N = %lld differs from the kept history (%lld)",
+                                  (long long)N, (long long)h->hist.n);
+  if (dtype != SP2_F64 && dtype != SP2_F32) return fail(h, SP2_EINVAL, "unknown dtype %d", dtype);
+  if (N == 0) return SP2_OK;
+  if (!G || !grad) return fail(h, SP2_EINVAL, "G or grad is NULL");
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const void* Gd;
+  TRY(stage_in(h, "B", G, mb, &Gd));
+  OutStage oy;
+  TRY(stage_out(h, "Y", grad, mb, &oy));
+  Ctx c;
+  TRY(make_ctx(h, h->hist.mode, h->hist.n, h->hist.np, true, &c));
+  TRY(run_adjoint(h, Gd, 1, 0, 1, dtype, oy.dev, dtype, c));
+  TRY(finish_out(h, oy));
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->M = h->hist.M;
+    info->converged = 1;
+    info->beta = h->hist.beta;
+    for (int i = 1; i <= h->hist.M; ++i) info->sigma[i - 1] = (int8_t)h->hist.sigma[i];
+  }
+  fill_timing(c, h->hist.M, info);
+  return SP2_OK;
+}
+
+int sp2_release_history(sp2_handle_t h) {
+  if (!h) return SP2_EINVAL;
+  h->hist.valid = false;
+  std::vector<std::string> names;
+  for (auto& kv : h->bufs)
+    if (kv.first.rfind("ckpt.", 0) == 0 || kv.first.rfind("seg.", 0) == 0) names.push_back(kv.first);
+  cudaStreamSynchronize(h->stream);
+  for (auto& nm : names) ws_free(h, nm);
+  return SP2_OK;
+}
+
+int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, int64_t K, int64_t N,
+                      int dtype, int q_diag_only, double* out) {
+  if (!h) return SP2_EINVAL;
+  if (L < 0 || K < 0 || N < 0) return fail(h, SP2_EINVAL, "negative size");
+  if (dtype != SP2_F64 && dtype != SP2_F32) return fail(h, SP2_EINVAL, "unknown dtype %d", dtype);
+  if (L == 0 || K == 0) return SP2_OK;
+  if (!out) return fail(h, SP2_EINVAL, "out is NULL");
+  if (N == 0) {
+    OutStage oo;
+    TRY(stage_out(h, "out", out, (size_t)L * K * sizeof(double), &oo));
+    CK(cudaMemsetAsync(oo.dev, 0, (size_t)L * K * sizeof(double), h->stream));
+    TRY(finish_out(h, oo));
+    CK(cudaStreamSynchronize(h->stream));
+    return SP2_OK;
+  }
+  if (!P || !Q) return fail(h, SP2_EINVAL, "P or Q is NULL");
+  const void *Pd, *Qd;
+  TRY(stage_in(h, "P", P, (size_t)L * N * N * dsize(dtype), &Pd));
+  TRY(stage_in(h, "Q", Q, (size_t)K * (q_diag_only ? N : N * N) * dsize(dtype), &Qd));
+  OutStage oo;
+  TRY(stage_out(h, "out", out, (size_t)L * K * sizeof(double), &oo));
+  const int np_ = contract_nparts(N, q_diag_only);
+  void* part;
+  TRY(ws(h, "contract.part", (size_t)L * K * np_ * sizeof(double), &part));
+  CK(launch_contract(Pd, L, Qd, K, N, dtype, q_diag_only, static_cast<double*>(part), np_,
+                     static_cast<double*>(oo.dev), h->stream));
+  TRY(finish_out(h, oo));
+  CK(cudaStreamSynchronize(h->stream));
+  return SP2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+"""The C ABI library builds, loads and exports what include/sp2.h declares
+(CPU only: no compute call is made here)."""
+import ctypes as C
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sp2.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2409_17033_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\**\s+\**([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sp2_density", "sp2_response", "sp2_susceptibility", "response_contract",
+                     "sp2_adjoint", "sp2_create", "sp2_destroy", "sp2_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    from paper_2409_17033_gb300 import _lib
+    assert set(_lib.EXPORTS) >= set(declared_functions())
+
+
+def test_nm_shows_c_linkage(lib):
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    from paper_2409_17033_gb300 import _lib
+    out = subprocess.run([nm, "-D", "--defined-only", _lib.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in declared_functions():
+        assert name in syms, f"{name} not exported with C linkage"
+
+
+def test_struct_layout_matches_c(tmp_path, lib):
+    """sizeof/offsetof of sp2_opts and sp2_info from a C compiler agree with
+    the ctypes mirror used by the binding."""
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2409_17033_gb300 import _lib
+    probe = tmp_path / "probe.c"
+    fields_o = [f for f, _ in _lib.Opts._fields_]
+    fields_i = [f for f, _ in _lib.Info._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){",
+             'printf("%zu %zu\\n", sizeof(sp2_opts), sizeof(sp2_info));']
+    for f in fields_o:
+        lines.append(f'printf("%zu\\n", offsetof(sp2_opts, {f}));')
+    for f in fields_i:
+        lines.append(f'printf("%zu\\n", offsetof(sp2_info, {f}));')
+    lines.append("return 0;}")
+    probe.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([gcc, str(probe), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals[0] == C.sizeof(_lib.Opts)
+    assert vals[1] == C.sizeof(_lib.Info)
+    offs = vals[2:]
+    for f, off in zip(fields_o, offs[:len(fields_o)]):
+        assert getattr(_lib.Opts, f).offset == off, f
+    for f, off in zip(fields_i, offs[len(fields_o):]):
+        assert getattr(_lib.Info, f).offset == off, f
+
+
+def test_default_opts_host_only(lib):
+    """sp2_default_opts is pure host code: callable without a GPU."""
+    from paper_2409_17033_gb300 import _lib
+    o = _lib.Opts()
+    lib.sp2_default_opts(C.byref(o))
+    assert o.mode == _lib.MODE_FP32
+    assert o.max_iter == 100 and o.min_iter == 4 and o.ckpt_k == 4
+    assert o.floor_gate == pytest.approx(0.1)
+    assert o.fixed_m == 0 and not o.sigma_in
+
+
+def test_null_handle_is_rejected(lib):
+    """Argument validation happens before any CUDA call."""
+    from paper_2409_17033_gb300 import _lib
+    assert lib.sp2_destroy(None) == _lib.EINVAL
+    assert lib.sp2_density(None, None, 4, 0, 2.0, None, None, None) == _lib.EINVAL
+    assert lib.sp2_create(None, None, 0) == _lib.EINVAL
