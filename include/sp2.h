@@ -80,19 +80,25 @@ typedef enum { SP2_F64 = 0, SP2_F32 = 1 } sp2_dtype;
  *   SP2_MODE_BF16X2  Eq. doubleHalf / Eq. MixPrecMult with bfloat16 hi/lo planes:
  *                    three tensor-core products (hi*hi + hi*lo + lo*hi, lo*lo
  *                    dropped, Eq. mults), FP32 accumulation, FP32 master copy.
+ *   SP2_MODE_FP16X2  the same with fp16 planes, the paper's own format: the lo
+ *                    plane holds the residual times 2^11 and is accumulated
+ *                    separately; response matrices carry a per-matrix
+ *                    power-of-two scale so that no plane entry exceeds 2^14.
  */
 typedef enum {
   SP2_MODE_FP64 = 0,
   SP2_MODE_FP32 = 1,
-  SP2_MODE_BF16X2 = 2
+  SP2_MODE_BF16X2 = 2,
+  SP2_MODE_FP16X2 = 3
 } sp2_mode;
 
 typedef struct {
   int mode;            /* sp2_mode */
   double idem_tol;     /* stop when |e_{n+1}| <= idem_tol; <= 0 disables this test.
                           e_n = Tr[X_n] - ||X_n||_F^2 is the idempotency error (Sec. II). */
-  double floor_gate;   /* precision-floor stop: after step n, stop when |e_{n-1}| <= floor_gate
-                          and |e_{n+1}| >= |e_{n-1}|; < 0 selects the default 0.1, 0 disables */
+  double floor_gate;   /* precision-floor stop on f_n = ||X_n - X_n^2||_F^2: after step n >= 3,
+                          stop when f_{n-2} <= floor_gate and f_n >= f_{n-2}
+                          (< 0 selects the default 0.03, 0 disables) */
   int max_iter;        /* cap on SP2 steps M (1..SP2_MAX_ITER; 0 = default 100) */
   int min_iter;        /* no stop test before this step (default 4 when < 0) */
   int fixed_m;         /* > 0: take exactly fixed_m steps with the branches in sigma_in */
@@ -115,6 +121,7 @@ typedef struct {
   double idem_err;     /* e of D = X_{M+1} */
   int8_t sigma[SP2_MAX_ITER];         /* sigma_1..sigma_M */
   double errors[SP2_MAX_ITER + 1];    /* e of X_1..X_{M+1} */
+  double idem_fro[SP2_MAX_ITER];      /* f = ||X_n - X_n^2||_F^2 of X_1..X_M */
   int64_t n_gemm_launches;            /* product-kernel launches that did work */
   double executed_flops;              /* tensor/FMA flops issued by the product kernels (FMA = 2) */
   double algorithmic_flops;           /* flops the products need by definition: the upper
@@ -128,7 +135,8 @@ typedef struct {
 
 typedef struct sp2_handle_s* sp2_handle_t;
 
-/* Fill *opts with defaults (mode FP32, idem_tol 0, floor_gate 0.1, max_iter 100, min_iter 4). */
+/* Fill *opts with defaults (mode FP32, idem_tol 0, floor_gate 0.03, max_iter 100, min_iter 4,
+ * ckpt_k 4). */
 void sp2_default_opts(sp2_opts* opts);
 
 /* Create a handle bound to the current CUDA device and `cuda_stream` (a

@@ -17,12 +17,18 @@ Readings where the paper is silent (the same readings the CUDA path takes):
   * branch choice: sigma = +1 (square) when |Tr[X^2] - N_occ| <= |Tr[2X - X^2] - N_occ|,
     ties go to squaring; Tr[X^2] is ||X||_F^2 for symmetric X (Sec. II asks
     for the trace of X_{n+1} closest to N_occ);
-  * stopping: with e_n = Tr[X_n] - ||X_n||_F^2 (the idempotency error,
-    sum of lambda (1 - lambda)), stop after step n >= min_iter when
-    |e_{n+1}| <= idem_tol, or when |e_{n-1}| <= floor_gate and
-    |e_{n+1}| >= |e_{n-1}| (the error stopped falling over a two-step
-    cycle: the precision floor). ``max_iter`` steps without either
-    condition is non-convergence.
+  * stopping: two idempotency errors are tracked, the trace form
+    e_n = Tr[X_n] - ||X_n||_F^2 (sum of lambda (1 - lambda)) and the squared
+    Frobenius form f_n = ||X_n - X_n^2||_F^2 (sum of lambda^2 (1 - lambda)^2),
+    f_n being known once step n has formed X_n^2. After step n >= min_iter
+    stop when |e_{n+1}| <= idem_tol (tolerance test), or when n >= 3,
+    f_{n-2} <= floor_gate and f_n >= f_{n-2} (the precision floor: in exact
+    arithmetic f falls monotonically over every two-step cycle once it is
+    below the gate, so a rise is rounding). The floor test uses f, not e:
+    in split low precision e carries a systematic trace bias of order
+    N times the unit roundoff that can exceed the true error of the
+    slowest (near-gap) eigenvalues, whereas f weights each eigenvalue by
+    its squared error. ``max_iter`` steps without either is non-convergence.
 """
 from __future__ import annotations
 
@@ -64,15 +70,22 @@ def traces(X: np.ndarray) -> tuple[float, float]:
     return float(np.trace(X)), float(np.sum(X * X.T))
 
 
-def stop_now(n: int, e: list[float], idem_tol: float, floor_gate: float,
+def idem_fro(X: np.ndarray, X2: np.ndarray) -> float:
+    """f = ||X - X^2||_F^2 given X and its square."""
+    d = X - X2
+    return float(np.sum(d * d))
+
+
+def stop_now(n: int, e: list[float], f: list[float], idem_tol: float, floor_gate: float,
              min_iter: int) -> bool:
-    """Stopping reading (module docstring). ``e[k]`` is the idempotency error
-    of X_{k+1}; after step n the newest entry is e[n] (X_{n+1})."""
+    """Stopping reading (module docstring). ``e[k]`` is the trace error of
+    X_{k+1} (after step n the newest is e[n], of X_{n+1}); ``f[k]`` is the
+    squared Frobenius error of X_{k+1} (after step n the newest is f[n-1], of X_n)."""
     if n < min_iter:
         return False
     if idem_tol > 0.0 and abs(e[n]) <= idem_tol:
         return True
-    if n >= 2 and floor_gate > 0.0 and abs(e[n - 2]) <= floor_gate and abs(e[n]) >= abs(e[n - 2]):
+    if n >= 3 and floor_gate > 0.0 and f[n - 3] <= floor_gate and f[n - 1] >= f[n - 3]:
         return True
     return False
 
@@ -84,6 +97,7 @@ class SP2Result:
     beta: float
     sigma: list[int]              # sigma_1..sigma_M
     errors: list[float]           # e for X_1..X_{M+1}
+    fro: list[float]              # f for X_1..X_M
     X: list[np.ndarray] | None    # X_1..X_M (inputs of each step) when kept
     converged: bool
 
@@ -93,7 +107,7 @@ class SP2Result:
 
 
 def sp2_density(H: np.ndarray, nocc: float, idem_tol: float = 1e-10,
-                max_iter: int = 100, min_iter: int = 4, floor_gate: float = 0.1,
+                max_iter: int = 100, min_iter: int = 4, floor_gate: float = 0.03,
                 sigma: list[int] | None = None, keep: bool = False,
                 bounds: tuple[float, float] | None = None) -> SP2Result:
     """SP2 recursive Fermi-operator expansion, Eq. DM0.
@@ -108,6 +122,7 @@ def sp2_density(H: np.ndarray, nocc: float, idem_tol: float = 1e-10,
     X = alpha * np.eye(n_) + beta * H
     t1, t2 = traces(X)
     errs = [t1 - t2]
+    fro: list[float] = []
     sig: list[int] = []
     hist: list[np.ndarray] | None = [] if keep else None
     converged = False
@@ -117,16 +132,17 @@ def sp2_density(H: np.ndarray, nocc: float, idem_tol: float = 1e-10,
         if keep:
             hist.append(X)
         X2 = X @ X
+        fro.append(idem_fro(X, X2))
         X = X2 if s > 0 else 2.0 * X - X2
         sig.append(int(s))
         t1, t2 = traces(X)
         errs.append(t1 - t2)
-        if sigma is None and stop_now(n, errs, idem_tol, floor_gate, min_iter):
+        if sigma is None and stop_now(n, errs, fro, idem_tol, floor_gate, min_iter):
             converged = True
             break
     if sigma is not None:
         converged = True
-    return SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs,
+    return SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs, fro=fro,
                      X=hist, converged=converged)
 
 
@@ -179,7 +195,7 @@ def merged_response(H: np.ndarray, nocc: float, B: np.ndarray, **kw):
     idem_tol = kw.get("idem_tol", 1e-10)
     max_iter = kw.get("max_iter", 100)
     min_iter = kw.get("min_iter", 4)
-    floor_gate = kw.get("floor_gate", 0.1)
+    floor_gate = kw.get("floor_gate", 0.03)
     sigma = kw.get("sigma")
     emin, emax = kw.get("bounds") or gershgorin_bounds(H)
     alpha, beta = sp2_scaling(emin, emax)
@@ -187,6 +203,7 @@ def merged_response(H: np.ndarray, nocc: float, B: np.ndarray, **kw):
     Y = [beta * b for b in Bs]
     t1, t2 = traces(X)
     errs = [t1 - t2]
+    fro: list[float] = []
     sig: list[int] = []
     converged = sigma is not None
     steps = len(sigma) if sigma is not None else max_iter
@@ -194,14 +211,15 @@ def merged_response(H: np.ndarray, nocc: float, B: np.ndarray, **kw):
         s = sigma[n - 1] if sigma is not None else choose_sigma(t1, t2, nocc)
         Y = [_response_step(y, X, s) for y in Y]
         X2 = X @ X
+        fro.append(idem_fro(X, X2))
         X = X2 if s > 0 else 2.0 * X - X2
         sig.append(int(s))
         t1, t2 = traces(X)
         errs.append(t1 - t2)
-        if sigma is None and stop_now(n, errs, idem_tol, floor_gate, min_iter):
+        if sigma is None and stop_now(n, errs, fro, idem_tol, floor_gate, min_iter):
             converged = True
             break
-    res = SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs,
+    res = SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs, fro=fro,
                     X=None, converged=converged)
     Yo = np.stack(Y)
     return res, (Yo[0] if single else Yo)

@@ -32,21 +32,35 @@ def round_fp16(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
 
 
-def split_hi_lo(x: np.ndarray, kind: str = "bf16", lo_scale: float = 1.0):
-    """Eq. doubleHalf. Returns (hi, lo) as float32 arrays holding narrow values.
-    ``lo_scale`` (a power of two) multiplies the residual before it is rounded
-    (FP16 range handling); the returned lo is the scaled one."""
+def pow2_scale(bound: float) -> float:
+    """Power-of-two matrix scale for FP16 planes: 2^(14 - e) where
+    bound = m 2^e with m in [0.5, 1), so every scaled entry is at most 2^14
+    (below the FP16 maximum 65504); 1 for a zero or non-finite bound."""
+    import math
+    if not (bound > 0.0) or not math.isfinite(bound):
+        return 1.0
+    _, e = math.frexp(float(np.float32(bound)))
+    k = min(120, max(-120, 14 - e))
+    return math.ldexp(1.0, k)
+
+
+def split_hi_lo(x: np.ndarray, kind: str = "bf16", lo_scale: float = 1.0, scale: float = 1.0):
+    """Eq. doubleHalf on scale * x. Returns (hi, lo) as float32 arrays holding
+    narrow values. ``scale`` and ``lo_scale`` are powers of two; lo_scale
+    multiplies the residual before it is rounded (FP16 range handling) and the
+    returned lo is the scaled one."""
     rnd = round_bf16 if kind == "bf16" else round_fp16
-    x32 = np.asarray(x, dtype=np.float32)
+    x32 = np.asarray(x, dtype=np.float32) * np.float32(scale)
     hi = rnd(x32)
     lo = rnd((x32 - hi) * np.float32(lo_scale))
     return hi, lo
 
 
 def mixed_product(X: np.ndarray, Y: np.ndarray, kind: str = "bf16",
-                  lo_scale: float = 1.0) -> np.ndarray:
-    """Eq. MixPrecMult without the lo*lo term, in FP64 on the split operands."""
-    xh, xl = split_hi_lo(X, kind, lo_scale)
-    yh, yl = split_hi_lo(Y, kind, lo_scale)
+                  lo_scale: float = 1.0, sx: float = 1.0, sy: float = 1.0) -> np.ndarray:
+    """Eq. MixPrecMult without the lo*lo term, in FP64 on the split operands
+    of sx X and sy Y, with the scales divided out."""
+    xh, xl = split_hi_lo(X, kind, lo_scale, sx)
+    yh, yl = split_hi_lo(Y, kind, lo_scale, sy)
     xh, xl, yh, yl = (a.astype(np.float64) for a in (xh, xl, yh, yl))
-    return xh @ yh + (xh @ yl + xl @ yh) / lo_scale
+    return (xh @ yh + (xh @ yl + xl @ yh) / lo_scale) / (sx * sy)

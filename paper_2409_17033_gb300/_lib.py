@@ -23,8 +23,8 @@ STATUS_NAMES = {0: "SP2_OK", 1: "SP2_EINVAL", 2: "SP2_ENOMEM", 3: "SP2_ENOCONV",
 # sp2_dtype
 F64, F32 = 0, 1
 # sp2_mode
-MODE_FP64, MODE_FP32, MODE_BF16X2 = 0, 1, 2
-MODES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16x2": MODE_BF16X2}
+MODE_FP64, MODE_FP32, MODE_BF16X2, MODE_FP16X2 = 0, 1, 2, 3
+MODES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16x2": MODE_BF16X2, "fp16x2": MODE_FP16X2}
 
 
 class Opts(C.Structure):
@@ -56,6 +56,7 @@ class Info(C.Structure):
         ("idem_err", C.c_double),
         ("sigma", C.c_int8 * SP2_MAX_ITER),
         ("errors", C.c_double * (SP2_MAX_ITER + 1)),
+        ("idem_fro", C.c_double * SP2_MAX_ITER),
         ("n_gemm_launches", C.c_int64),
         ("executed_flops", C.c_double),
         ("algorithmic_flops", C.c_double),
@@ -77,6 +78,7 @@ class Info(C.Structure):
             "idem_err": self.idem_err,
             "sigma": [int(self.sigma[i]) for i in range(m)],
             "errors": [float(self.errors[i]) for i in range(m + 1)],
+            "idem_fro": [float(self.idem_fro[i]) for i in range(m)],
             "n_gemm_launches": int(self.n_gemm_launches),
             "executed_flops": float(self.executed_flops),
             "algorithmic_flops": float(self.algorithmic_flops),

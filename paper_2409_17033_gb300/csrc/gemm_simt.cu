@@ -26,7 +26,7 @@ template <> struct Vec<double> { using type = double2; static constexpr int n = 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(256)
 k_gemm_simt(const T* __restrict__ A, const T* __restrict__ X, int64_t np, int epi,
-            T* __restrict__ out, const T* __restrict__ xprev, double2* __restrict__ part,
+            T* __restrict__ out, const T* __restrict__ xprev, Part3* __restrict__ part,
             const Tile* __restrict__ tiles, const DevState* st, int step) {
   static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
   using V = typename Vec<T>::type;
@@ -93,37 +93,42 @@ k_gemm_simt(const T* __restrict__ A, const T* __restrict__ X, int64_t np, int ep
   }
 
   const int sg = st->sigma[step];
-  double t1 = 0.0, t2 = 0.0;
+  double t1 = 0.0, t2 = 0.0, f = 0.0;
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int64_t gi = t.row0 + ty + i * (BM / TM), gj = t.col0 + tx + j * (BN / TN);
       if (gi > gj) continue;
-      T v = acc[i][j];
-      if (sg < 0) v = (T)2 * xprev[gi * np + gj] - v;
+      const T c = acc[i][j];
+      const T x = xprev[gi * np + gj];
+      const T v = sg > 0 ? c : (T)2 * x - c;
       out[gi * np + gj] = v;
       const double d = (double)v;
+      const double r = (double)x - (double)c;  // (X_n - X_n^2)_ij
       if (gi == gj) {
         t1 += d;
         t2 += d * d;
+        f += r * r;
       } else {
         out[gj * np + gi] = v;
         t2 += 2.0 * d * d;
+        f += 2.0 * r * r;
       }
     }
-  // block reduction of the trace partials (fixed order)
-  __shared__ double r1[8], r2[8];
+  // block reduction of the partials (fixed order)
+  __shared__ double r1[8], r2[8], r3[8];
   for (int o = 16; o > 0; o >>= 1) {
     t1 += __shfl_xor_sync(0xffffffffu, t1, o);
     t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    f += __shfl_xor_sync(0xffffffffu, f, o);
   }
-  if ((tid & 31) == 0) { r1[tid >> 5] = t1; r2[tid >> 5] = t2; }
+  if ((tid & 31) == 0) { r1[tid >> 5] = t1; r2[tid >> 5] = t2; r3[tid >> 5] = f; }
   __syncthreads();
   if (tid == 0) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int w = 0; w < 8; ++w) { s1 += r1[w]; s2 += r2[w]; }
-    part[blockIdx.x] = make_double2(s1, s2);
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int w = 0; w < 8; ++w) { s1 += r1[w]; s2 += r2[w]; s3 += r3[w]; }
+    part[blockIdx.x] = Part3{s1, s2, s3};
   }
 }
 
@@ -135,7 +140,7 @@ void simt_tile_shape(int mode, int* bm, int* bn) {
 }
 
 cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, const void* X,
-                             int64_t np, void* out, const void* x_prev, double2* part,
+                             int64_t np, void* out, const void* x_prev, Part3* part,
                              const Tile* tiles, int ntiles, const DevState* st, int step,
                              cudaStream_t s) {
   (void)a_rows;

@@ -3,10 +3,15 @@
 // Computes C = A X for the SP2 path with the hi/lo splitting of Eq. doubleHalf
 // and the three-product form of Eq. MixPrecMult / Eq. mults (lo*lo dropped):
 //     A X ~ A_hi X_hi + A_hi X_lo + A_lo X_hi,
-// evaluated as ONE accumulation over a concatenated K axis of length 3 np,
+// evaluated over a concatenated K axis of length 3 np,
 //     [A_hi | A_hi | A_lo] . [X_hi ; X_lo ; X_hi],
-// into an FP32 accumulator in tensor memory. X is symmetric, so the row-major
+// into FP32 accumulators in tensor memory. X is symmetric, so the row-major
 // X planes are directly the K-major B operand.
+//   BF16X2: one accumulator for all three segments.
+//   FP16X2: the lo planes hold residuals times 2^11, so segment 0 (hi*hi) and
+//           segments 1-2 (hi*lo, lo*hi) go to two accumulators (512 TMEM
+//           columns) combined as acc0 + 2^-11 acc1; A may carry a per-matrix
+//           power-of-two scale that the epilogue divides out.
 //
 // CTA tile 128 x 256, K step 64 (one 128-byte swizzle row of bf16), 4-stage
 // TMA -> shared-memory ring guarded by mbarriers. Warp roles:
@@ -39,14 +44,17 @@ constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NUM_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t ACC_COLS = 256;   // one 128 x 256 FP32 accumulator
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
-// Instruction descriptor, kind::f16: D=F32 (bits 4-5 = 1), A=BF16 (bits 7-9 = 1),
-// B=BF16 (bits 10-12 = 1), both K-major (bits 15,16 = 0), N>>3 at bit 17, M>>4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D=F32 (bits 4-5 = 1), A and B format at
+// bits 7-9 / 10-12 (BF16 = 1, F16 = 0; always the same for A and B), both
+// K-major (bits 15,16 = 0), N>>3 at bit 17, M>>4 at bit 24.
+constexpr uint32_t idesc_for(bool f16) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -159,20 +167,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void store_split(float* m, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                            int64_t idx, float v) {
-  m[idx] = v;
-  __nv_bfloat16 h = __float2bfloat16_rn(v);
+template <bool F16>
+__device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* lo, int64_t idx, float v) {
+  uint16_t h, l;
+  if (F16) split_fp16(v, 1.0f, h, l);
+  else split_bf16(v, h, l);
   hi[idx] = h;
-  lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  lo[idx] = l;
 }
 
+template <bool F16>
+__device__ __forceinline__ void store_split(float* m, uint16_t* hi, uint16_t* lo, int64_t idx,
+                                            float v) {
+  m[idx] = v;
+  split_store<F16>(hi, lo, idx, v);
+}
+
+template <bool F16>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
           const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-          int nkb, int epi, int64_t np, float* __restrict__ out, __nv_bfloat16* __restrict__ out_hi,
-          __nv_bfloat16* __restrict__ out_lo, const float* __restrict__ xprev,
-          double2* __restrict__ part, const Tile* __restrict__ tiles, DevState* st, int step) {
+          int nkb, int epi, int64_t np, float* __restrict__ out, uint16_t* __restrict__ out_hi,
+          uint16_t* __restrict__ out_lo, const float* __restrict__ xprev,
+          Part3* __restrict__ part, const Tile* __restrict__ tiles, DevState* st, int step,
+          const float* __restrict__ a_scale, float* __restrict__ zmax) {
+  constexpr uint32_t TMEM_COLS = F16 ? 2 * ACC_COLS : ACC_COLS;
+  constexpr uint32_t kIdesc = idesc_for(F16);
   {
     const int m = *((volatile const int*)&st->stop_at);
     if ((m != 0 && step > m) || *((volatile const int*)&st->abort_flag)) return;
@@ -184,7 +204,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
   uint64_t* empty = full + STAGES;
   uint64_t* accf = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
-  __shared__ double red1[4], red2[4];
+  __shared__ double red1[4], red2[4], red3[4];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Tile t = tiles[blockIdx.x];
@@ -247,11 +267,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
         const uint64_t adesc = sdesc_sw128(a_addr);
         const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
+        // FP16X2: segment 0 -> accumulator 0, segments 1-2 -> accumulator 1
+        const bool acc1 = F16 && kb >= nkb;
+        const uint32_t dtm = acc1 ? tmem + ACC_COLS : tmem;
+        const int kfirst = acc1 ? nkb : 0;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
-          // advance 16 bf16 = 32 bytes along K inside the swizzled row: +2 in 16-byte units
-          umma_bf16(tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
-                    (kb > 0 || k > 0) ? 1u : 0u);
+          // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
+          umma_bf16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                    (kb > kfirst || k > 0) ? 1u : 0u);
         }
         umma_commit(&empty[s]);
       }
@@ -265,35 +289,56 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
     bool ok = mbar_wait(accf, 0, abortf);
     ok = __all_sync(0xffffffffu, ok);
     tc_fence_after();
-    double t1 = 0.0, t2 = 0.0;
+    double t1 = 0.0, t2 = 0.0, f = 0.0;
     if (ok && !*((volatile int*)abortf)) {
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
       const int sg = (epi == EPI_SQUARE) ? st->sigma[step] : 1;
+      const int64_t bat = gi / np;  // batch entry of this row (stacked A)
+      const float inv_s = (F16 && a_scale) ? 1.0f / a_scale[bat] : 1.0f;
+      float zm = 0.0f;
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(trow + (uint32_t)c0, v);
         float val[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) val[j] = __uint_as_float(v[j]);
+        if (F16) {
+          uint32_t w[16];
+          tmem_ld16(trow + ACC_COLS + (uint32_t)c0, w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            val[j] = (val[j] + __uint_as_float(w[j]) * (1.0f / kLoScale)) * inv_s;
+        }
         const int64_t gj0 = t.col0 + c0;
         if (epi == EPI_PLAIN) {
           float4* dst = reinterpret_cast<float4*>(out + gi * np + gj0);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             dst[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
+          if (zmax) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) zm = fmaxf(zm, fabsf(val[j]));
+          }
           continue;
         }
         if (gj0 + 15 < gi) continue;  // whole chunk below the diagonal
-        if (sg < 0) {
+        float xin[16];  // X_n: the 2X - X^2 branch and the Frobenius idempotency error
+        {
           const float4* xp = reinterpret_cast<const float4*>(xprev + gi * np + gj0);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             float4 x = xp[j];
-            val[4 * j + 0] = 2.0f * x.x - val[4 * j + 0];
-            val[4 * j + 1] = 2.0f * x.y - val[4 * j + 1];
-            val[4 * j + 2] = 2.0f * x.z - val[4 * j + 2];
-            val[4 * j + 3] = 2.0f * x.w - val[4 * j + 3];
+            xin[4 * j + 0] = x.x;
+            xin[4 * j + 1] = x.y;
+            xin[4 * j + 2] = x.z;
+            xin[4 * j + 3] = x.w;
           }
+        }
+        float res[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          res[j] = xin[j] - val[j];
+          if (sg < 0) val[j] = 2.0f * xin[j] - val[j];
         }
         if (gj0 >= gi) {
           // whole chunk on or above the diagonal: vector stores
@@ -301,11 +346,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             dm[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
-          __align__(16) __nv_bfloat16 h[16], l[16];
+          __align__(16) uint16_t h[16], l[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            h[j] = __float2bfloat16_rn(val[j]);
-            l[j] = __float2bfloat16_rn(val[j] - __bfloat162float(h[j]));
+            if (F16) split_fp16(val[j], 1.0f, h[j], l[j]);
+            else split_bf16(val[j], h[j], l[j]);
           }
           uint4* dh = reinterpret_cast<uint4*>(out_hi + gi * np + gj0);
           uint4* dl = reinterpret_cast<uint4*>(out_lo + gi * np + gj0);
@@ -316,31 +361,41 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (gj0 + j >= gi) store_split(out, out_hi, out_lo, gi * np + gj0 + j, val[j]);
+            if (gj0 + j >= gi) store_split<F16>(out, out_hi, out_lo, gi * np + gj0 + j, val[j]);
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int64_t gj = gj0 + j;
           if (gj < gi) continue;
           const double d = (double)val[j];
+          const double r = (double)res[j];
           if (gj == gi) {
             t1 += d;
             t2 += d * d;
+            f += r * r;
           } else {
-            store_split(out, out_hi, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
+            store_split<F16>(out, out_hi, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
             t2 += 2.0 * d * d;
+            f += 2.0 * r * r;
           }
         }
+      }
+      if (epi == EPI_PLAIN && zmax) {
+        for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+        if (lane == 0 && zm > 0.0f)
+          atomicMax(reinterpret_cast<int*>(&zmax[bat]), __float_as_int(zm));
       }
     }
     if (epi == EPI_SQUARE) {
       for (int o = 16; o > 0; o >>= 1) {
         t1 += __shfl_xor_sync(0xffffffffu, t1, o);
         t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+        f += __shfl_xor_sync(0xffffffffu, f, o);
       }
       if (lane == 0) {
         red1[q] = t1;
         red2[q] = t2;
+        red3[q] = f;
       }
     }
   }
@@ -348,8 +403,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
   tc_fence_before();
   __syncthreads();
   if (epi == EPI_SQUARE && threadIdx.x == 0)
-    part[blockIdx.x] = make_double2(red1[0] + red1[1] + red1[2] + red1[3],
-                                    red2[0] + red2[1] + red2[2] + red2[3]);
+    part[blockIdx.x] = Part3{red1[0] + red1[1] + red1[2] + red1[3],
+                             red2[0] + red2[1] + red2[2] + red2[3],
+                             red3[0] + red3[1] + red3[2] + red3[3]};
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -377,17 +433,18 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 2D map over a row-major bf16 plane (rows x np), box = 64 columns x box_rows rows.
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int box_rows) {
+// 2D map over a row-major 16-bit plane (rows x np), box = 64 columns x box_rows rows.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int box_rows, bool f16) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)np * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -398,16 +455,20 @@ void tc_tile_shape(int* bm, int* bn) {
   *bn = BN;
 }
 
-cudaError_t launch_gemm_tc(int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
-                           const float* x_prev, double2* part, const Tile* tiles, int ntiles,
-                           DevState* st, int step, cudaStream_t s, char* errbuf, size_t errlen) {
+cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
+                           const float* x_prev, Part3* part, const Tile* tiles, int ntiles,
+                           DevState* st, int step, const float* a_scale, float* zmax,
+                           cudaStream_t s, char* errbuf, size_t errlen) {
   if (ntiles <= 0) return cudaSuccess;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+  const bool f16 = mode == SP2_MODE_FP16X2;
+  static bool attr_done[2] = {false, false};
+  if (!attr_done[f16]) {
+    cudaError_t e = f16 ? cudaFuncSetAttribute(k_gemm_tc<true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
+                        : cudaFuncSetAttribute(k_gemm_tc<false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_done[f16] = true;
   }
   // TMA box/stride rules: 16-byte aligned bases, np*2-byte row pitch (np % 256 == 0),
   // every x coordinate a multiple of 64 elements.
@@ -418,15 +479,20 @@ cudaError_t launch_gemm_tc(int epi, TcOperand A, TcOperand B, int64_t np, MatBuf
     return cudaErrorInvalidValue;
   }
   CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
-  if (!make_map(&ma_hi, A.hi, A.rows, np, BM) || !make_map(&ma_lo, A.lo, A.rows, np, BM) ||
-      !make_map(&mb_hi, B.hi, B.rows, np, BN) || !make_map(&mb_lo, B.lo, B.rows, np, BN)) {
+  if (!make_map(&ma_hi, A.hi, A.rows, np, BM, f16) || !make_map(&ma_lo, A.lo, A.rows, np, BM, f16) ||
+      !make_map(&mb_hi, B.hi, B.rows, np, BN, f16) || !make_map(&mb_lo, B.lo, B.rows, np, BN, f16)) {
     snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     return cudaErrorInvalidValue;
   }
   const int nkb = (int)(np / BK);
-  k_gemm_tc<<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
-      ma_hi, ma_lo, mb_hi, mb_lo, nkb, epi, np, static_cast<float*>(out.master), out.hi, out.lo,
-      x_prev, part, tiles, st, step);
+  if (f16)
+    k_gemm_tc<true><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
+        ma_hi, ma_lo, mb_hi, mb_lo, nkb, epi, np, static_cast<float*>(out.master), out.hi, out.lo,
+        x_prev, part, tiles, st, step, a_scale, zmax);
+  else
+    k_gemm_tc<false><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
+        ma_hi, ma_lo, mb_hi, mb_lo, nkb, epi, np, static_cast<float*>(out.master), out.hi, out.lo,
+        x_prev, part, tiles, st, step, nullptr, nullptr);
   return cudaGetLastError();
 }
 

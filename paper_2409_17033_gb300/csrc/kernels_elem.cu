@@ -91,17 +91,25 @@ __global__ void k_bounds_final(const double2* part, int nparts, DevState* st) {
 }
 
 // ------------------------------------------------------------ init
-__device__ __forceinline__ void store_elem(MatBuf d, int mode, int64_t idx, double v) {
+// Writes one element in the mode's layout; split modes also write the planes
+// (fp16 planes with scale 1) unless planes == false.
+__device__ __forceinline__ void store_elem(MatBuf d, int mode, int64_t idx, double v, bool planes) {
   if (mode == SP2_MODE_FP64) {
     static_cast<double*>(d.master)[idx] = v;
-  } else {
-    float f = (float)v;
-    static_cast<float*>(d.master)[idx] = f;
-    if (mode == SP2_MODE_BF16X2) {
-      __nv_bfloat16 h = __float2bfloat16_rn(f);
-      d.hi[idx] = h;
-      d.lo[idx] = __float2bfloat16_rn(f - __bfloat162float(h));
-    }
+    return;
+  }
+  const float f = (float)v;
+  static_cast<float*>(d.master)[idx] = f;
+  if (!planes) return;
+  uint16_t h, l;
+  if (mode == SP2_MODE_BF16X2) {
+    split_bf16(f, h, l);
+    d.hi[idx] = h;
+    d.lo[idx] = l;
+  } else if (mode == SP2_MODE_FP16X2) {
+    split_fp16(f, 1.0f, h, l);
+    d.hi[idx] = h;
+    d.lo[idx] = l;
   }
 }
 
@@ -109,13 +117,20 @@ __device__ __forceinline__ double stored_value(int mode, double v) {
   return mode == SP2_MODE_FP64 ? v : (double)(float)v;
 }
 
+// atomic max of non-negative floats through their (monotone) bit patterns
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
+  atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
+}
+
 __global__ void k_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
                        int diag_only, int symmetrize, double alpha, double beta, int mode,
-                       MatBuf dst, double2* part) {
+                       MatBuf dst, Part3* part, float* ymax) {
   double t1 = 0.0, t2 = 0.0;
+  const bool planes = !(mode == SP2_MODE_FP16X2 && ymax != nullptr);
   const int64_t rows = batch * np;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const int64_t b = r / np, i = r % np;
+    float rmax = 0.0f;
     for (int64_t j = threadIdx.x; j < np; j += blockDim.x) {
       double v = 0.0;
       if (i < n && j < n) {
@@ -129,35 +144,44 @@ __global__ void k_init(const void* src, int64_t n, int64_t np, int64_t batch, in
         }
         if (i == j) v += alpha;
       }
-      store_elem(dst, mode, r * np + j, v);
+      store_elem(dst, mode, r * np + j, v, planes);
       double s = stored_value(mode, v);
       if (i == j) t1 += s;
       t2 += s * s;
+      rmax = fmaxf(rmax, fabsf((float)v));
+    }
+    if (!planes) {
+      for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      if ((threadIdx.x & 31) == 0 && rmax > 0.0f) atomic_max_nonneg(&ymax[b], rmax);
     }
   }
   if (part) {
     t1 = block_sum(t1);
     __syncthreads();
     t2 = block_sum(t2);
-    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(t1, t2);
+    if (threadIdx.x == 0) part[blockIdx.x] = Part3{t1, t2, 0.0};
   }
 }
 
 // ------------------------------------------------------------ decide
-__global__ void k_decide(const double2* part, DevState* st, DecideParams p) {
-  double t1 = 0.0, t2 = 0.0;
+__global__ void k_decide(const Part3* part, DevState* st, DecideParams p) {
+  double t1 = 0.0, t2 = 0.0, f = 0.0;
   for (int i = threadIdx.x; i < p.nparts; i += blockDim.x) {
-    t1 += part[i].x;
-    t2 += part[i].y;
+    t1 += part[i].t1;
+    t2 += part[i].t2;
+    f += part[i].f;
   }
   t1 = block_sum(t1);
   __syncthreads();
   t2 = block_sum(t2);
+  __syncthreads();
+  f = block_sum(f);
   if (threadIdx.x != 0) return;
   if (st->stop_at != 0) return;  // already stopped: later steps are no-ops
   const int n = p.n;
   st->t1[n] = t1;
   st->t2[n] = t2;
+  if (n >= 2) st->f[n - 1] = f;  // the step that produced X_n measured X_{n-1}
   if (!isfinite(t1) || !isfinite(t2)) {
     st->nonfinite = 1;
     st->stop_at = (n - 1 >= 1) ? n - 1 : -1;
@@ -172,10 +196,10 @@ __global__ void k_decide(const double2* part, DevState* st, DecideParams p) {
     const double e = fabs(t1 - t2);
     bool stop = false;
     if (p.idem_tol > 0.0 && e <= p.idem_tol) stop = true;
-    if (!stop && s >= 2 && p.floor_gate > 0.0) {
-      const double e2 = fabs(st->t1[n - 2] - st->t2[n - 2]);
-      if (e2 <= p.floor_gate && e >= e2) stop = true;
-    }
+    // precision floor on f: f_{s-2} <= gate and f_s >= f_{s-2}
+    if (!stop && s >= 3 && p.floor_gate > 0.0 && st->f[s - 2] <= p.floor_gate &&
+        st->f[s] >= st->f[s - 2])
+      stop = true;
     if (stop) {
       st->stop_at = s;
       return;
@@ -194,8 +218,25 @@ __device__ __forceinline__ bool halted(const DevState* st, int step) {
 // Y_{n+1} = (1 - sigma) Y_n + sigma (Z + Z^T), Z = Y_n X_n (Eqs. DM1-DM3: X_n Y_n = (Y_n X_n)^T
 // for symmetric X_n, Y_n). One block per 32x32 tile pair (I <= J); both tiles written.
 template <typename ZT, int MODE>
+__device__ __forceinline__ void store_y(MatBuf y, int64_t idx, ZT v, float s) {
+  static_cast<ZT*>(y.master)[idx] = v;
+  if (MODE == SP2_MODE_BF16X2) {
+    uint16_t h, l;
+    split_bf16((float)v, h, l);
+    y.hi[idx] = h;
+    y.lo[idx] = l;
+  } else if (MODE == SP2_MODE_FP16X2) {
+    uint16_t h, l;
+    split_fp16((float)v, s, h, l);
+    y.hi[idx] = h;
+    y.lo[idx] = l;
+  }
+}
+
+template <typename ZT, int MODE>
 __global__ void k_symm_update(const ZT* __restrict__ Z, MatBuf yin, MatBuf yout, int64_t np,
-                              const DevState* st, int step) {
+                              const DevState* st, int step, ScaleBuf sc, int slot_in,
+                              int slot_out) {
   if (halted(st, step)) return;
   const int I = blockIdx.y, J = blockIdx.x;
   if (I > J) return;
@@ -206,42 +247,45 @@ __global__ void k_symm_update(const ZT* __restrict__ Z, MatBuf yin, MatBuf yout,
   __shared__ ZT yt[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int sg = st->sigma[step];
+  float s = 1.0f;
+  if (MODE == SP2_MODE_FP16X2) {
+    // |Y_{n+1}| <= |Z_ij| + |Z_ji| (+ 2 |Y_n| for sigma<0), elementwise
+    float bound = 2.0f * sc.zmax[b];
+    if (sg < 0) bound += 2.0f * sc.ymax[slot_in * sc.B + b];
+    s = pow2_scale(bound);
+    if (I == 0 && J == 0 && tx == 0 && ty == 0) sc.yscale[slot_out * sc.B + b] = s;
+  }
   for (int k = 0; k < 32; k += 8) {
     zij[ty + k][tx] = Z[base + (int64_t)(I * 32 + ty + k) * np + J * 32 + tx];
     zji[ty + k][tx] = Z[base + (int64_t)(J * 32 + ty + k) * np + I * 32 + tx];
   }
   __syncthreads();
+  float amax = 0.0f;
   for (int k = 0; k < 32; k += 8) {
     const int r = ty + k, c = tx;
     const int64_t idx = base + (int64_t)(I * 32 + r) * np + J * 32 + c;
-    ZT s = zij[r][c] + zji[c][r];
+    ZT sum = zij[r][c] + zji[c][r];
     ZT y;
     if (sg > 0) {
-      y = s;
+      y = sum;
     } else {
       ZT yo = static_cast<const ZT*>(yin.master)[idx];
-      y = (ZT)2 * yo - s;
+      y = (ZT)2 * yo - sum;
     }
     yt[r][c] = y;
-    static_cast<ZT*>(yout.master)[idx] = y;
-    if (MODE == SP2_MODE_BF16X2) {
-      __nv_bfloat16 h = __float2bfloat16_rn((float)y);
-      yout.hi[idx] = h;
-      yout.lo[idx] = __float2bfloat16_rn((float)y - __bfloat162float(h));
-    }
+    store_y<ZT, MODE>(yout, idx, y, s);
+    amax = fmaxf(amax, fabsf((float)y));
+  }
+  if (MODE == SP2_MODE_FP16X2) {
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (tx == 0 && amax > 0.0f) atomic_max_nonneg(&sc.ymax[slot_out * sc.B + b], amax);
   }
   if (I == J) return;
   __syncthreads();
   for (int k = 0; k < 32; k += 8) {
     const int r = ty + k, c = tx;
     const int64_t idx = base + (int64_t)(J * 32 + r) * np + I * 32 + c;
-    ZT y = yt[c][r];
-    static_cast<ZT*>(yout.master)[idx] = y;
-    if (MODE == SP2_MODE_BF16X2) {
-      __nv_bfloat16 h = __float2bfloat16_rn((float)y);
-      yout.hi[idx] = h;
-      yout.lo[idx] = __float2bfloat16_rn((float)y - __bfloat162float(h));
-    }
+    store_y<ZT, MODE>(yout, idx, yt[c][r], s);
   }
 }
 
@@ -261,13 +305,32 @@ __global__ void k_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int
   }
 }
 
-__global__ void k_split(MatBuf m, int64_t total) {
+__global__ void k_split(MatBuf m, int64_t total, int mode) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    float f = static_cast<const float*>(m.master)[t];
-    __nv_bfloat16 h = __float2bfloat16_rn(f);
+    const float f = static_cast<const float*>(m.master)[t];
+    uint16_t h, l;
+    if (mode == SP2_MODE_BF16X2) split_bf16(f, h, l);
+    else split_fp16(f, 1.0f, h, l);
     m.hi[t] = h;
-    m.lo[t] = __float2bfloat16_rn(f - __bfloat162float(h));
+    m.lo[t] = l;
+  }
+}
+
+__global__ void k_scales_from_max(ScaleBuf sc, int slot) {
+  for (int64_t b = threadIdx.x; b < sc.B; b += blockDim.x)
+    sc.yscale[slot * sc.B + b] = pow2_scale(sc.ymax[slot * sc.B + b]);
+}
+
+__global__ void k_split_scaled(MatBuf m, int64_t per, ScaleBuf sc, int slot) {
+  const int64_t total = per * sc.B;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float f = static_cast<const float*>(m.master)[t];
+    uint16_t h, l;
+    split_fp16(f, sc.yscale[slot * sc.B + t / per], h, l);
+    m.hi[t] = h;
+    m.lo[t] = l;
   }
 }
 
@@ -333,30 +396,34 @@ int init_nparts(int64_t np) { return (int)(np < 1024 ? np : 1024); }
 
 cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
                         int diag_only, int symmetrize, double alpha, double beta, int mode,
-                        MatBuf dst, double2* part, int nparts, cudaStream_t s) {
+                        MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s) {
   int grid = part ? nparts : grid_for(batch * np, 1, 4096);
   k_init<<<grid, kRedThreads, 0, s>>>(src, n, np, batch, dtype, diag_only, symmetrize, alpha,
-                                      beta, mode, dst, part);
+                                      beta, mode, dst, part, ymax);
   return cudaGetLastError();
 }
 
-cudaError_t launch_decide(const double2* part, DevState* st, DecideParams p, cudaStream_t s) {
+cudaError_t launch_decide(const Part3* part, DevState* st, DecideParams p, cudaStream_t s) {
   k_decide<<<1, kRedThreads, 0, s>>>(part, st, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t np, int64_t batch,
-                               int mode, const DevState* st, int step, cudaStream_t s) {
+                               int mode, const DevState* st, int step, ScaleBuf sc, int slot_in,
+                               int slot_out, cudaStream_t s) {
   dim3 grid((unsigned)(np / 32), (unsigned)(np / 32), (unsigned)batch), block(32, 8);
   if (mode == SP2_MODE_FP64)
-    k_symm_update<double, SP2_MODE_FP64><<<grid, block, 0, s>>>(static_cast<const double*>(Z), y_in,
-                                                                y_out, np, st, step);
+    k_symm_update<double, SP2_MODE_FP64><<<grid, block, 0, s>>>(
+        static_cast<const double*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
   else if (mode == SP2_MODE_FP32)
-    k_symm_update<float, SP2_MODE_FP32><<<grid, block, 0, s>>>(static_cast<const float*>(Z), y_in,
-                                                               y_out, np, st, step);
+    k_symm_update<float, SP2_MODE_FP32><<<grid, block, 0, s>>>(
+        static_cast<const float*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
+  else if (mode == SP2_MODE_BF16X2)
+    k_symm_update<float, SP2_MODE_BF16X2><<<grid, block, 0, s>>>(
+        static_cast<const float*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
   else
-    k_symm_update<float, SP2_MODE_BF16X2><<<grid, block, 0, s>>>(static_cast<const float*>(Z), y_in,
-                                                                 y_out, np, st, step);
+    k_symm_update<float, SP2_MODE_FP16X2><<<grid, block, 0, s>>>(
+        static_cast<const float*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
   return cudaGetLastError();
 }
 
@@ -367,8 +434,14 @@ cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, cudaStream_t s) {
-  k_split<<<grid_for(rows * np, 256, 8192), 256, 0, s>>>(m, rows * np);
+cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, int mode, cudaStream_t s) {
+  k_split<<<grid_for(rows * np, 256, 8192), 256, 0, s>>>(m, rows * np, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_scaled(MatBuf m, int64_t np, ScaleBuf sc, int slot, cudaStream_t s) {
+  k_scales_from_max<<<1, 256, 0, s>>>(sc, slot);
+  k_split_scaled<<<grid_for(sc.B * np * np, 256, 8192), 256, 0, s>>>(m, np * np, sc, slot);
   return cudaGetLastError();
 }
 

@@ -118,13 +118,25 @@ int mat(sp2_handle_t h, const std::string& name, int64_t rows, int64_t np, int m
   const size_t cnt = (size_t)rows * (size_t)np;
   *m = MatBuf{};
   TRY(ws(h, name + ".m", cnt * master_size(mode), &m->master));
-  if (mode == SP2_MODE_BF16X2) {
+  if (split_mode(mode)) {
     void* p;
     TRY(ws(h, name + ".h", cnt * 2, &p));
-    m->hi = static_cast<__nv_bfloat16*>(p);
+    m->hi = static_cast<uint16_t*>(p);
     TRY(ws(h, name + ".l", cnt * 2, &p));
-    m->lo = static_cast<__nv_bfloat16*>(p);
+    m->lo = static_cast<uint16_t*>(p);
   }
+  return SP2_OK;
+}
+
+// FP16X2 per-matrix scale state for a batch of B response matrices
+int scales(sp2_handle_t h, const std::string& name, int64_t B, ScaleBuf* sc) {
+  void* p;
+  TRY(ws(h, name, (size_t)B * 5 * sizeof(float), &p));
+  float* f = static_cast<float*>(p);
+  sc->ymax = f;
+  sc->yscale = f + 2 * B;
+  sc->zmax = f + 4 * B;
+  sc->B = B;
   return SP2_OK;
 }
 
@@ -178,7 +190,7 @@ size_t dsize(int dtype) { return dtype == SP2_F64 ? 8 : 4; }
 
 // --------------------------------------------------------------- tile lists
 void tile_shape(int mode, int* bm, int* bn) {
-  if (mode == SP2_MODE_BF16X2) tc_tile_shape(bm, bn);
+  if (split_mode(mode)) tc_tile_shape(bm, bn);
   else simt_tile_shape(mode, bm, bn);
 }
 
@@ -226,7 +238,7 @@ struct Ctx {
   int64_t n;      // caller's matrix size
   int64_t np;     // padded size
   DevState* st;
-  double2* part;  // trace partials (>= max tiles)
+  Part3* part;    // trace / idempotency partials (>= max tiles)
   int64_t launches = 0;   // product launches that did work
   double flops = 0.0;     // executed product flops
   double alg = 0.0;       // algorithmic product flops
@@ -268,7 +280,7 @@ int64_t timed_count(const Ctx& c, int m) {
   return k;
 }
 
-double k_mult(int mode) { return mode == SP2_MODE_BF16X2 ? 3.0 : 1.0; }
+double k_mult(int mode) { return split_mode(mode) ? 3.0 : 1.0; }
 
 // X_{n+1} = sigma_n>0 ? X_n^2 : 2 X_n - X_n^2, with trace partials; returns #partials
 int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* nparts) {
@@ -283,11 +295,12 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
     TRY(ev_pair(c, &e0, &e1));
     CK(cudaEventRecord(e0, h->stream));
   }
-  if (c.mode == SP2_MODE_BF16X2) {
+  if (split_mode(c.mode)) {
     char eb[256] = {0};
     TcOperand a{xin.hi, xin.lo, c.np};
-    cudaError_t e = launch_gemm_tc(EPI_SQUARE, a, a, c.np, xout, static_cast<const float*>(xin.master),
-                                   c.part, tl, nt, c.st, step, h->stream, eb, sizeof eb);
+    cudaError_t e = launch_gemm_tc(c.mode, EPI_SQUARE, a, a, c.np, xout,
+                                   static_cast<const float*>(xin.master), c.part, tl, nt, c.st,
+                                   step, nullptr, nullptr, h->stream, eb, sizeof eb);
     if (e != cudaSuccess) return fail(h, SP2_ECUDA, "square product: %s %s", cudaGetErrorString(e), eb);
   } else {
     CK(launch_gemm_simt(c.mode, EPI_SQUARE, xin.master, c.np, xin.master, c.np, xout.master,
@@ -307,7 +320,7 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
 
 // Y_{n+1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n) for a batch of Y
 int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout, int64_t batch,
-                  int step) {
+                  int step, const ScaleBuf& sc, int slot_in, int slot_out) {
   sp2_handle_t h = c.h;
   const int64_t rows = batch * c.np;
   void* z;
@@ -322,13 +335,16 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
     TRY(ev_pair(c, &e0, &e1));
     CK(cudaEventRecord(e0, h->stream));
   }
-  if (c.mode == SP2_MODE_BF16X2) {
+  const bool f16 = c.mode == SP2_MODE_FP16X2;
+  if (f16) CK(cudaMemsetAsync(sc.zmax, 0, sizeof(float) * batch, h->stream));
+  if (split_mode(c.mode)) {
     char eb[256] = {0};
     TcOperand a{yin.hi, yin.lo, rows}, b{x.hi, x.lo, c.np};
     MatBuf zo;
     zo.master = z;
-    cudaError_t e = launch_gemm_tc(EPI_PLAIN, a, b, c.np, zo, nullptr, c.part, tl, nt, c.st, step,
-                                   h->stream, eb, sizeof eb);
+    cudaError_t e = launch_gemm_tc(c.mode, EPI_PLAIN, a, b, c.np, zo, nullptr, c.part, tl, nt, c.st,
+                                   step, f16 ? sc.yscale + slot_in * sc.B : nullptr,
+                                   f16 ? sc.zmax : nullptr, h->stream, eb, sizeof eb);
     if (e != cudaSuccess) return fail(h, SP2_ECUDA, "response product: %s %s", cudaGetErrorString(e), eb);
   } else {
     CK(launch_gemm_simt(c.mode, EPI_PLAIN, yin.master, rows, x.master, c.np, z, nullptr, c.part,
@@ -338,7 +354,9 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
     CK(cudaEventRecord(e1, h->stream));
     c.timed.push_back({step, 0});
   }
-  CK(launch_symm_update(z, yin, yout, c.np, batch, c.mode, c.st, step, h->stream));
+  if (f16) CK(cudaMemsetAsync(sc.ymax + slot_out * sc.B, 0, sizeof(float) * batch, h->stream));
+  CK(launch_symm_update(z, yin, yout, c.np, batch, c.mode, c.st, step, sc, slot_in, slot_out,
+                        h->stream));
   c.launches++;
   c.kernels += 2;
   c.flops += 2.0 * bm * bn * (double)c.np * k_mult(c.mode) * nt;
@@ -347,7 +365,8 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
 }
 
 int validate_opts(sp2_handle_t h, const sp2_opts* o) {
-  if (o->mode != SP2_MODE_FP64 && o->mode != SP2_MODE_FP32 && o->mode != SP2_MODE_BF16X2)
+  if (o->mode != SP2_MODE_FP64 && o->mode != SP2_MODE_FP32 && o->mode != SP2_MODE_BF16X2 &&
+      o->mode != SP2_MODE_FP16X2)
     return fail(h, SP2_EINVAL, "unknown mode %d", o->mode);
   if (o->max_iter < 1 || o->max_iter > SP2_MAX_ITER)
     return fail(h, SP2_EINVAL, "max_iter %d outside 1..%d", o->max_iter, SP2_MAX_ITER);
@@ -367,7 +386,7 @@ sp2_opts resolve(const sp2_opts* in) {
   if (in) o = *in;
   if (o.max_iter == 0) o.max_iter = 100;
   if (o.min_iter < 0) o.min_iter = 4;
-  if (o.floor_gate < 0) o.floor_gate = 0.1;
+  if (o.floor_gate < 0) o.floor_gate = 0.03;
   if (o.ckpt_k == 0) o.ckpt_k = 4;
   return o;
 }
@@ -444,7 +463,8 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   TRY(mat(h, "X0", np, np, mode, &X[0]));
   TRY(mat(h, "X1", np, np, mode, &X[1]));
   const int ni = init_nparts(np);
-  CK(launch_init(Hd, n, np, 1, dtype, 0, 0, alpha, beta, mode, X[1], c.part, ni, h->stream));
+  CK(launch_init(Hd, n, np, 1, dtype, 0, 0, alpha, beta, mode, X[1], c.part, ni, nullptr,
+                 h->stream));
   c.kernels++;
   DecideParams dp;
   dp.nocc = nocc;
@@ -457,11 +477,22 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   dp.nparts = ni;
   CK(launch_decide(c.part, c.st, dp, h->stream));
   c.kernels++;
+  ScaleBuf sc;
   if (ybatch > 0) {
     TRY(mat(h, "Y0", ybatch * np, np, mode, &Y[0]));
     TRY(mat(h, "Y1", ybatch * np, np, mode, &Y[1]));
-    CK(launch_init(Bd, n, np, ybatch, dtype, b_diag, 0, 0.0, beta, mode, Y[1], nullptr, 0, h->stream));
+    const bool f16 = mode == SP2_MODE_FP16X2;
+    if (f16) {
+      TRY(scales(h, "Y.scale", ybatch, &sc));
+      CK(cudaMemsetAsync(sc.ymax, 0, sizeof(float) * 2 * ybatch, h->stream));
+    }
+    CK(launch_init(Bd, n, np, ybatch, dtype, b_diag, 0, 0.0, beta, mode, Y[1], nullptr, 0,
+                   f16 ? sc.ymax + 1 * ybatch : nullptr, h->stream));
     c.kernels++;
+    if (f16) {
+      CK(launch_split_scaled(Y[1], np, sc, 1, h->stream));
+      c.kernels += 2;
+    }
   }
 
   const int maxit = o.fixed_m > 0 ? o.fixed_m : o.max_iter;
@@ -481,7 +512,9 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
       TRY(ws(h, "ckpt." + std::to_string((step - 1) / o.ckpt_k), xbytes, &ck));
       CK(cudaMemcpyAsync(ck, xin.master, xbytes, cudaMemcpyDeviceToDevice, h->stream));
     }
-    if (ybatch > 0) TRY(response_step(c, xin, Y[step % 2], Y[(step + 1) % 2], ybatch, step));
+    if (ybatch > 0)
+      TRY(response_step(c, xin, Y[step % 2], Y[(step + 1) % 2], ybatch, step, sc, step % 2,
+                        (step + 1) % 2));
     int nparts = 0;
     TRY(square_step(c, xin, xo, step, &nparts));
     dp.n = step + 1;
@@ -527,6 +560,7 @@ void fill_info(sp2_handle_t h, const Sp2Out& r, const Ctx& c, sp2_info* info) {
   const DevState& s = *h->h_state;
   for (int i = 1; i <= r.M; ++i) info->sigma[i - 1] = (int8_t)s.sigma[i];
   for (int i = 1; i <= r.M + 1; ++i) info->errors[i - 1] = s.t1[i] - s.t2[i];
+  for (int i = 1; i <= r.M; ++i) info->idem_fro[i - 1] = s.f[i];
   info->trace = s.t1[r.M + 1];
   info->idem_err = s.t1[r.M + 1] - s.t2[r.M + 1];
   info->n_gemm_launches = c.launches;
@@ -560,8 +594,8 @@ int make_ctx(sp2_handle_t h, int mode, int64_t n, int64_t np, bool timing, Ctx* 
   int64_t maxp = (np / bm) * (np / bn) + 8;
   if (maxp < init_nparts(np)) maxp = init_nparts(np);
   void* p;
-  TRY(ws(h, "part", (size_t)maxp * sizeof(double2), &p));
-  c->part = static_cast<double2*>(p);
+  TRY(ws(h, "part", (size_t)maxp * sizeof(Part3), &p));
+  c->part = static_cast<Part3*>(p);
   return SP2_OK;
 }
 
@@ -587,9 +621,19 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
   TRY(mat(h, "G0", batch * np, np, mode, &G[0]));
   TRY(mat(h, "G1", batch * np, np, mode, &G[1]));
   int gs = (M + 1) % 2;  // slot of G_{M+1}
+  ScaleBuf sc;
+  const bool f16 = mode == SP2_MODE_FP16X2;
+  if (f16) {
+    TRY(scales(h, "G.scale", batch, &sc));
+    CK(cudaMemsetAsync(sc.ymax, 0, sizeof(float) * 2 * batch, h->stream));
+  }
   CK(launch_init(Bd, n, np, batch, dtype, b_diag, symmetrize, 0.0, 1.0, mode, G[gs], nullptr, 0,
-                 h->stream));
+                 f16 ? sc.ymax + gs * batch : nullptr, h->stream));
   c.kernels++;
+  if (f16) {
+    CK(launch_split_scaled(G[gs], np, sc, gs, h->stream));
+    c.kernels += 2;
+  }
   std::vector<MatBuf> seg(k);
   for (int i = 0; i < k; ++i) TRY(mat(h, "seg." + std::to_string(i), np, np, mode, &seg[i]));
   const size_t xbytes = (size_t)np * np * master_size(mode);
@@ -600,8 +644,8 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
     void* ck;
     TRY(ws(h, "ckpt." + std::to_string(j), xbytes, &ck));
     CK(cudaMemcpyAsync(seg[0].master, ck, xbytes, cudaMemcpyDeviceToDevice, h->stream));
-    if (mode == SP2_MODE_BF16X2) {
-      CK(launch_split(seg[0], np, np, h->stream));
+    if (split_mode(mode)) {
+      CK(launch_split(seg[0], np, np, mode, h->stream));
       c.kernels++;
     }
     for (int s = s0; s < s1; ++s) {
@@ -609,7 +653,7 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
       TRY(square_step(c, seg[s - s0], seg[s - s0 + 1], s, &nparts));
     }
     for (int s = s1; s >= s0; --s) {
-      TRY(response_step(c, seg[s - s0], G[gs], G[1 - gs], batch, s));
+      TRY(response_step(c, seg[s - s0], G[gs], G[1 - gs], batch, s, sc, gs, 1 - gs));
       gs = 1 - gs;
     }
   }
@@ -630,7 +674,7 @@ void sp2_default_opts(sp2_opts* o) {
   memset(o, 0, sizeof *o);
   o->mode = SP2_MODE_FP32;
   o->idem_tol = 0.0;
-  o->floor_gate = 0.1;
+  o->floor_gate = 0.03;
   o->max_iter = 100;
   o->min_iter = 4;
   o->fixed_m = 0;

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "../../include/sp2.h"
@@ -23,6 +24,7 @@ inline int64_t pad_n(int64_t n) { return (n + kPad - 1) / kPad * kPad; }
 struct DevState {
   double t1[SP2_MAX_ITER + 2];   // Tr[X_n], index n = 1..M+1
   double t2[SP2_MAX_ITER + 2];   // ||X_n||_F^2
+  double f[SP2_MAX_ITER + 2];    // ||X_n - X_n^2||_F^2, known after step n
   int sigma[SP2_MAX_ITER + 2];   // sigma_n, the branch taken by step n (X_n -> X_{n+1})
   int stop_at;                   // M once a stop rule fired, else 0
   int nonfinite;                 // a trace was NaN/Inf
@@ -33,14 +35,64 @@ struct DevState {
 
 // Storage of one padded matrix (or a batch of them) in a given mode.
 struct MatBuf {
-  void* master = nullptr;        // double (FP64 mode) or float, rows x np
-  __nv_bfloat16* hi = nullptr;   // BF16X2 only: hi plane
-  __nv_bfloat16* lo = nullptr;   // BF16X2 only: lo plane
+  void* master = nullptr;        // double (FP64 mode) or float, rows x np, unscaled
+  uint16_t* hi = nullptr;        // split modes: hi plane (bf16 or fp16 bits)
+  uint16_t* lo = nullptr;        // split modes: lo plane
+};
+
+inline bool split_mode(int mode) { return mode == SP2_MODE_BF16X2 || mode == SP2_MODE_FP16X2; }
+
+// Eq. doubleHalf with bfloat16: hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void split_bf16(float v, uint16_t& h, uint16_t& l) {
+  const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+  const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+  h = __bfloat16_as_ushort(hb);
+  l = __bfloat16_as_ushort(lb);
+}
+
+// The fp16 lo plane holds the residual times 2^11 (one fp16 significand), so
+// it stays out of the subnormal range; products with it are scaled back by
+// 2^-11 from a separate accumulator.
+constexpr float kLoScale = 2048.0f;
+
+// Eq. doubleHalf with fp16 on s * v (s a power of two chosen per matrix so
+// that |s v| <= 2^14 < 65504): hi = fp16(s v), lo = fp16((s v - hi) * 2^11).
+__device__ __forceinline__ void split_fp16(float v, float s, uint16_t& h, uint16_t& l) {
+  const float vs = v * s;
+  const __half hh = __float2half_rn(vs);
+  const __half ll = __float2half_rn((vs - __half2float(hh)) * kLoScale);
+  h = __half_as_ushort(hh);
+  l = __half_as_ushort(ll);
+}
+
+// Power-of-two plane scale for a matrix whose entries are bounded by `bound`:
+// 2^(14 - e) with bound <= 2^e, so every scaled entry is at most 2^14.
+__device__ __forceinline__ float pow2_scale(float bound) {
+  if (!(bound > 0.0f) || !isfinite(bound)) return 1.0f;
+  int e;
+  frexpf(bound, &e);
+  int k = 14 - e;
+  k = k < -120 ? -120 : (k > 120 ? 120 : k);
+  return ldexpf(1.0f, k);
+}
+
+// Per-matrix scale state of a batch of B response matrices (FP16X2 only).
+struct ScaleBuf {
+  float* ymax = nullptr;    // [2][B] max |Y| of the matrix in each ping-pong slot
+  float* yscale = nullptr;  // [2][B] power-of-two scale of each slot's fp16 planes
+  float* zmax = nullptr;    // [B]    max |Z| of the current step's product Z = Y X
+  int64_t B = 0;
 };
 
 enum Epi : int {
   EPI_SQUARE = 0,   // out = sigma>0 ? C : 2 X - C, symmetric (upper tiles, mirrored), traces
   EPI_PLAIN = 1,    // out = C (fp32/fp64 Z), all tiles
+};
+
+// Per-block partial sums written by the kernels that produce an X_{n+1}:
+// t1 = Tr[X_{n+1}], t2 = ||X_{n+1}||_F^2, f = ||X_n - X_n^2||_F^2.
+struct Part3 {
+  double t1, t2, f;
 };
 
 struct Tile {       // one output tile of a product kernel
@@ -57,9 +109,12 @@ int bounds_nparts(int64_t n);
 // X_1 = alpha I + beta H (or Y_1 = beta B for a batch), caller layout -> padded mode layout.
 // diag_only: B given as diagonals (batch x n). symmetrize: use (B + B^T)/2.
 // part (nullable): trace partials, one per block.
+// FP16X2: planes are written with scale 1 when ymax is null (X), otherwise only
+// the master is written and max|entry| per batch entry is accumulated into
+// ymax (planes follow from launch_split_scaled).
 cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
                         int diag_only, int symmetrize, double alpha, double beta, int mode,
-                        MatBuf dst, double2* part, int nparts, cudaStream_t s);
+                        MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s);
 int init_nparts(int64_t np);
 
 // reduce trace partials of X_n, decide stop/sigma (see DevState)
@@ -70,18 +125,23 @@ struct DecideParams {
   int min_iter, max_iter;
   int fixed_m;       // > 0: sigma preset, stop when n - 1 == fixed_m
 };
-cudaError_t launch_decide(const double2* part, DevState* st, DecideParams p, cudaStream_t s);
+cudaError_t launch_decide(const Part3* part, DevState* st, DecideParams p, cudaStream_t s);
 
 // Y_{n+1} = sigma>0 ? Z + Z^T : 2 Y - (Z + Z^T) for a batch; step n reads sigma_n.
+// FP16X2: the planes of Y_{n+1} use the scale bounded by 2 max|Z| (+ 2 max|Y_n|
+// when sigma<0) from sc (slots slot_in -> slot_out); max|Y_{n+1}| is recorded.
 cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t np, int64_t batch,
-                               int mode, const DevState* st, int step, cudaStream_t s);
+                               int mode, const DevState* st, int step, ScaleBuf sc, int slot_in,
+                               int slot_out, cudaStream_t s);
 
 // padded mode layout -> caller layout (N x N per batch entry), times `scale`
 cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
                             double scale, void* dst, int dtype, cudaStream_t s);
 
-// regenerate hi/lo planes from the FP32 master (BF16X2), rows x np
-cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, cudaStream_t s);
+// regenerate hi/lo planes from the FP32 master, rows x np (plane scale 1)
+cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, int mode, cudaStream_t s);
+// FP16X2 batch of B matrices: scale of slot `slot` from its ymax, then planes
+cudaError_t launch_split_scaled(MatBuf m, int64_t np, ScaleBuf sc, int slot, cudaStream_t s);
 
 // response_contract
 cudaError_t launch_contract(const void* P, int64_t L, const void* Q, int64_t K, int64_t n,
@@ -92,20 +152,23 @@ int contract_nparts(int64_t n, int q_diag);
 // product kernels
 // SIMT (FP64 / FP32): C = A * X with A rows x np (stacked), X np x np symmetric.
 cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, const void* X,
-                             int64_t np, void* out, const void* x_prev, double2* part,
+                             int64_t np, void* out, const void* x_prev, Part3* part,
                              const Tile* tiles, int ntiles, const DevState* st, int step,
                              cudaStream_t s);
 void simt_tile_shape(int mode, int* bm, int* bn);
 
-// tcgen05 split-precision (BF16X2)
+// tcgen05 split-precision (BF16X2 / FP16X2)
 struct TcOperand {   // hi/lo planes of a stacked operand, rows x np
-  const __nv_bfloat16* hi;
-  const __nv_bfloat16* lo;
+  const uint16_t* hi;
+  const uint16_t* lo;
   int64_t rows;
 };
-cudaError_t launch_gemm_tc(int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
-                           const float* x_prev, double2* part, const Tile* tiles, int ntiles,
-                           DevState* st, int step, cudaStream_t s, char* errbuf, size_t errlen);
+// a_scale (FP16X2, EPI_PLAIN): per batch entry of A, the plane scale to divide
+// out; zmax (FP16X2, EPI_PLAIN): per batch entry, receives max |Z|.
+cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
+                           const float* x_prev, Part3* part, const Tile* tiles, int ntiles,
+                           DevState* st, int step, const float* a_scale, float* zmax,
+                           cudaStream_t s, char* errbuf, size_t errlen);
 void tc_tile_shape(int* bm, int* bn);
 
 }  // namespace sp2

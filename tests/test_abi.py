@@ -92,7 +92,7 @@ def test_default_opts_host_only(lib):
     lib.sp2_default_opts(C.byref(o))
     assert o.mode == _lib.MODE_FP32
     assert o.max_iter == 100 and o.min_iter == 4 and o.ckpt_k == 4
-    assert o.floor_gate == pytest.approx(0.1)
+    assert o.floor_gate == pytest.approx(0.03)
     assert o.fixed_m == 0 and not o.sigma_in
 
 

@@ -62,6 +62,8 @@ def test_fp64_density_matches_oracle(sp2, c1):
     assert info["trace"] == pytest.approx(p.nocc, abs=1e-8)
     for a, b in zip(info["errors"], o.errors):
         assert a == pytest.approx(b, rel=1e-8, abs=1e-12)
+    for a, b in zip(info["idem_fro"], o.fro):
+        assert a == pytest.approx(b, rel=1e-6, abs=1e-20)
 
 
 def test_fp64_susceptibility_forward_backward(sp2, c1):
@@ -165,6 +167,60 @@ def test_bf16x2_single_response_step_matches_emulated_split(sp2, c1):
         assert rel(host(chi[0]), ref) < 2e-6
 
 
+def test_fp16x2_single_steps_match_emulated_split(sp2, c1):
+    """FP16X2: one square step and one response step against Eq. MixPrecMult on
+    fp16 planes (lo scaled by 2^11, Y with its power-of-two plane scale)."""
+    p, _ = c1
+    H = cuda(p.H, torch.float32)
+    for s in (1, -1):
+        D, info = sp2.sp2_density(H, p.nocc, mode="fp16x2", sigma=[s])
+        a, b = info["alpha"], info["beta"]
+        X1 = (a * np.eye(128) + b * p.H.astype(np.float32).astype(np.float64)).astype(np.float32)
+        P = split.mixed_product(X1, X1, "fp16", lo_scale=2048.0)
+        ref = P if s > 0 else 2.0 * X1.astype(np.float64) - P
+        assert rel(host(D), ref) < 1e-6
+        chi, _, _ = sp2.sp2_susceptibility(H, p.nocc, cuda(p.A[None], torch.float32), "forward",
+                                           mode="fp16x2", sigma=[s])
+        Y1 = (b * p.A.astype(np.float32).astype(np.float64)).astype(np.float32)
+        sy = split.pow2_scale(float(np.max(np.abs(Y1))))
+        Z = split.mixed_product(Y1, X1, "fp16", lo_scale=2048.0, sx=sy)
+        Pz = Z + Z.T
+        ref = Pz if s > 0 else 2.0 * Y1.astype(np.float64) - Pz
+        assert rel(host(chi[0]), ref) < 1e-6
+
+
+def test_fp16x2_large_response_entries_do_not_overflow(sp2, c1):
+    """Observables with entries far beyond the FP16 range (1e6) still give the
+    exact response up to the split precision (per-matrix plane scales)."""
+    p, _ = c1
+    H = cuda(p.H, torch.float32)
+    A = p.A * 1e6
+    chi, _, info = sp2.sp2_susceptibility(H, p.nocc, cuda(A[None], torch.float32), "backward",
+                                          mode="fp16x2")
+    c = host(chi[0])
+    assert np.isfinite(c).all()
+    assert rel(c, exact.response_zero_T(p.e, p.Q, p.nocc, A)) < 1e-3
+
+
+@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2"])
+def test_split_modes_converged_against_closed_forms(sp2, c1, mode):
+    p, _ = c1
+    H = cuda(p.H, torch.float32)
+    A = cuda(p.A[None], torch.float32)
+    tolD, tolC = (1e-4, 1e-2) if mode == "bf16x2" else (1e-5, 1e-3)
+    chi_b, D, info = sp2.sp2_susceptibility(H, p.nocc, A, "backward", mode=mode, want_density=True)
+    chi_f, _, _ = sp2.sp2_susceptibility(H, p.nocc, A, "forward", mode=mode)
+    assert info["converged"]
+    D_ex = exact.density_zero_T(p.e, p.Q, p.nocc)
+    chi_ex = exact.response_zero_T(p.e, p.Q, p.nocc, p.A)
+    assert rel(host(D), D_ex) < tolD
+    assert rel(host(chi_b[0]), chi_ex) < tolC
+    assert rel(host(chi_f[0]), chi_ex) < tolC
+    D1, _, _ = sp2.sp2_response(H, p.nocc, cuda(p.H1, torch.float32), mode=mode)
+    for k in range(3):
+        assert rel(host(D1[k]), exact.response_zero_T(p.e, p.Q, p.nocc, p.H1[k])) < tolC
+
+
 def test_bf16x2_converged_against_closed_forms(sp2, c1):
     p, _ = c1
     H = cuda(p.H, torch.float32)
@@ -185,7 +241,7 @@ def test_bf16x2_converged_against_closed_forms(sp2, c1):
 
 # ------------------------------------------------------------------ ragged sizes / edges
 @pytest.mark.parametrize("n", [1, 17, 130, 300])
-@pytest.mark.parametrize("mode", ["fp64", "bf16x2"])
+@pytest.mark.parametrize("mode", ["fp64", "bf16x2", "fp16x2"])
 def test_ragged_sizes(sp2, n, mode):
     nocc = max(1, n // 3) if n > 1 else 1
     p = workloads.random_spectrum(n, nocc=nocc, k=1, seed=n)
@@ -193,7 +249,7 @@ def test_ragged_sizes(sp2, n, mode):
     chi, D, info = sp2.sp2_susceptibility(cuda(p.H, dt), p.nocc, cuda(p.A[None], dt), "backward",
                                           mode=mode, want_density=True,
                                           idem_tol=1e-10 if mode == "fp64" else 0.0)
-    tolD, tolC = (1e-10, 1e-8) if mode == "fp64" else (1e-4, 1e-2)
+    tolD, tolC = {"fp64": (1e-10, 1e-8), "bf16x2": (1e-4, 1e-2), "fp16x2": (1e-5, 1e-3)}[mode]
     assert rel(host(D), exact.density_zero_T(p.e, p.Q, p.nocc)) < tolD
     chi_ex = exact.response_zero_T(p.e, p.Q, p.nocc, p.A)
     if np.linalg.norm(chi_ex) > 0:

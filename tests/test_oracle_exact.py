@@ -148,3 +148,24 @@ def test_mixed_product_accuracy():
     # lo scaling by a power of two leaves the product unchanged up to rounding
     a = split.mixed_product(X, Y, "fp16", lo_scale=2.0 ** 12)
     assert rel(a, ref) < 1e-6
+
+
+def test_pow2_scale_keeps_fp16_range():
+    for b in (1e-30, 3e-8, 0.7, 1.0, 17.0, 1e5, 6.5e4):
+        s = split.pow2_scale(b)
+        assert np.log2(s) == int(np.log2(s))
+        assert 2.0 ** 13 <= b * s <= 2.0 ** 14
+    assert split.pow2_scale(0.0) == 1.0 and split.pow2_scale(float("nan")) == 1.0
+
+
+def test_scaled_fp16_split_product():
+    """A power-of-two plane scale changes nothing but the range: the product of
+    scaled splits equals the unscaled one where neither under- nor overflows,
+    and it rescues entries that would overflow FP16."""
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (64, 64))
+    Y = rng.uniform(-1, 1, (64, 64)) * 1e6          # overflows FP16 unscaled
+    s = split.pow2_scale(np.max(np.abs(Y)))
+    P = split.mixed_product(Y, X, "fp16", lo_scale=2048.0, sx=s)
+    assert np.isfinite(P).all()
+    assert np.linalg.norm(P - Y @ X) / np.linalg.norm(Y @ X) < 1e-6

@@ -79,6 +79,49 @@ def test_sp2_finite_m_matches_scalar_recursion(cfg1):
     assert rel(rr.D, D_ref) < 1e-12
 
 
+def test_frobenius_idempotency_error_closed_form(cfg1):
+    """f_n = ||X_n - X_n^2||_F^2 = sum_i x_i^2 (1 - x_i)^2 over the eigenvalues
+    x_i of X_n (finite-M eigenvalue reference)."""
+    p = cfg1
+    r = sp2.sp2_density(p.H, p.nocc, idem_tol=1e-10)
+    xs = exact.sp2_scalar(r.alpha + r.beta * p.e, r.sigma)
+    for n in range(r.M):
+        x = xs[n]
+        ref = float(np.sum(x * x * (1 - x) ** 2))
+        assert r.fro[n] == pytest.approx(ref, rel=1e-9, abs=1e-22)
+
+
+def test_floor_rule_in_emulated_split_precision():
+    """With X kept in FP32 and products in the split form of Eq. MixPrecMult,
+    the floor test stops only after the slow near-gap eigenvalues have
+    converged (f has fallen to the rounding floor, far below the gate) and
+    the result matches the exact projector to the accuracy the split form
+    allows at this gap (about 1.3e-4 here; the scaled gap is 4.5e-3)."""
+    from oracle import split
+    tb = workloads.tight_binding(512, seed=0)
+    e, V = exact.eigh(tb.H)
+    emin, emax = sp2.gershgorin_bounds(tb.H)
+    a, b = sp2.sp2_scaling(emin, emax)
+    X = (a * np.eye(512) + b * tb.H).astype(np.float32).astype(np.float64)
+    fro, errs = [], [sp2.traces(X)[0] - sp2.traces(X)[1]]
+    M = None
+    for n in range(1, 100):
+        t1, t2 = sp2.traces(X)
+        s = sp2.choose_sigma(t1, t2, tb.nocc)
+        X2 = split.mixed_product(X, X, "bf16")
+        fro.append(sp2.idem_fro(X, X2))
+        X = (X2 if s > 0 else 2 * X - X2).astype(np.float32).astype(np.float64)
+        t1, t2 = sp2.traces(X)
+        errs.append(t1 - t2)
+        if sp2.stop_now(n, errs, fro, 0.0, 0.03, 4):
+            M = n
+            break
+    assert M is not None
+    assert min(fro) < 1e-7 and fro[M - 3] < 1e-6
+    D = exact.density_zero_T(e, V, tb.nocc)
+    assert np.linalg.norm(X - D) / np.linalg.norm(D) < 3e-4
+
+
 def test_stop_rule_reaches_tolerance_and_floor(cfg1):
     p = cfg1
     r = sp2.sp2_density(p.H, p.nocc, idem_tol=1e-10)
