@@ -96,9 +96,13 @@ typedef struct {
   int mode;            /* sp2_mode */
   double idem_tol;     /* stop when |e_{n+1}| <= idem_tol; <= 0 disables this test.
                           e_n = Tr[X_n] - ||X_n||_F^2 is the idempotency error (Sec. II). */
-  double floor_gate;   /* precision-floor stop on f_n = ||X_n - X_n^2||_F^2: after step n >= 3,
-                          stop when f_{n-2} <= floor_gate and f_n >= f_{n-2}
-                          (< 0 selects the default 0.03, 0 disables) */
+  double floor_gate;   /* precision-floor stop on f_n = ||X_n - X_n^2||_F^2 (< 0 selects the
+                          default 0.03, 0 disables). After step n it fires when steps n-2 and
+                          n-1 took opposite branches, f_{n-2} <= floor_gate and f_n >= f_{n-2},
+                          or when the smallest f so far is <= floor_gate and none of the last
+                          4 steps went below it. In exact arithmetic neither happens once
+                          f <= 0.03 (every eigenvalue is within 1/4 of 0 or 1 and a pair of
+                          opposite branches maps a distance d to at most 4 d^2). */
   int max_iter;        /* cap on SP2 steps M (1..SP2_MAX_ITER; 0 = default 100) */
   int min_iter;        /* no stop test before this step (default 4 when < 0) */
   int fixed_m;         /* > 0: take exactly fixed_m steps with the branches in sigma_in */

@@ -21,20 +21,30 @@ Readings where the paper is silent (the same readings the CUDA path takes):
     e_n = Tr[X_n] - ||X_n||_F^2 (sum of lambda (1 - lambda)) and the squared
     Frobenius form f_n = ||X_n - X_n^2||_F^2 (sum of lambda^2 (1 - lambda)^2),
     f_n being known once step n has formed X_n^2. After step n >= min_iter
-    stop when |e_{n+1}| <= idem_tol (tolerance test), or when n >= 3,
-    f_{n-2} <= floor_gate and f_n >= f_{n-2} (the precision floor: in exact
-    arithmetic f falls monotonically over every two-step cycle once it is
-    below the gate, so a rise is rounding). The floor test uses f, not e:
-    in split low precision e carries a systematic trace bias of order
-    N times the unit roundoff that can exceed the true error of the
-    slowest (near-gap) eigenvalues, whereas f weights each eigenvalue by
-    its squared error. ``max_iter`` steps without either is non-convergence.
+    stop when |e_{n+1}| <= idem_tol (tolerance test), or when n >= 3, the
+    two steps n-2, n-1 took opposite branches, f_{n-2} <= floor_gate and
+    f_n >= f_{n-2}, or when the smallest f so far is <= floor_gate and none
+    of the last STALL = 4 steps went below it (the precision floor).
+    Why these mark a floor: a pair of opposite branches maps an eigenvalue
+    at distance d from 0 or 1 to one at distance at most 4 d^2, so once every
+    d < 1/4 (guaranteed by f <= 0.03 < (3/16)^2) f must fall over such a
+    pair in exact arithmetic, and over any four steps it reaches a new
+    minimum; a rise or a stall is rounding. Pairs of equal branches alone
+    are not tested: they double d on one side, so f may rise legitimately.
+    The test uses f, not e: with split low-precision products e carries a
+    systematic trace bias of order N times the unit roundoff that can
+    exceed the true error of the slow near-gap eigenvalues, whereas f
+    weights every eigenvalue by its squared error. ``max_iter`` steps
+    without any test firing is non-convergence.
 """
 from __future__ import annotations
 
 import dataclasses
 
 import numpy as np
+
+
+STALL = 4  # steps without a new minimum of f that mark the precision floor
 
 
 # ---------------------------------------------------------------- Sec. II
@@ -76,17 +86,24 @@ def idem_fro(X: np.ndarray, X2: np.ndarray) -> float:
     return float(np.sum(d * d))
 
 
-def stop_now(n: int, e: list[float], f: list[float], idem_tol: float, floor_gate: float,
-             min_iter: int) -> bool:
+def stop_now(n: int, e: list[float], f: list[float], sig: list[int], idem_tol: float,
+             floor_gate: float, min_iter: int) -> bool:
     """Stopping reading (module docstring). ``e[k]`` is the trace error of
     X_{k+1} (after step n the newest is e[n], of X_{n+1}); ``f[k]`` is the
-    squared Frobenius error of X_{k+1} (after step n the newest is f[n-1], of X_n)."""
+    squared Frobenius error of X_{k+1} (after step n the newest is f[n-1], of
+    X_n); ``sig[k]`` is sigma_{k+1}."""
     if n < min_iter:
         return False
     if idem_tol > 0.0 and abs(e[n]) <= idem_tol:
         return True
-    if n >= 3 and floor_gate > 0.0 and f[n - 3] <= floor_gate and f[n - 1] >= f[n - 3]:
+    if floor_gate <= 0.0:
+        return False
+    if n >= 3 and sig[n - 3] != sig[n - 2] and f[n - 3] <= floor_gate and f[n - 1] >= f[n - 3]:
         return True
+    if n > STALL:
+        best = min(f[:n - STALL])
+        if best <= floor_gate and min(f[n - STALL:n]) >= best:
+            return True
     return False
 
 
@@ -137,7 +154,7 @@ def sp2_density(H: np.ndarray, nocc: float, idem_tol: float = 1e-10,
         sig.append(int(s))
         t1, t2 = traces(X)
         errs.append(t1 - t2)
-        if sigma is None and stop_now(n, errs, fro, idem_tol, floor_gate, min_iter):
+        if sigma is None and stop_now(n, errs, fro, sig, idem_tol, floor_gate, min_iter):
             converged = True
             break
     if sigma is not None:
@@ -216,7 +233,7 @@ def merged_response(H: np.ndarray, nocc: float, B: np.ndarray, **kw):
         sig.append(int(s))
         t1, t2 = traces(X)
         errs.append(t1 - t2)
-        if sigma is None and stop_now(n, errs, fro, idem_tol, floor_gate, min_iter):
+        if sigma is None and stop_now(n, errs, fro, sig, idem_tol, floor_gate, min_iter):
             converged = True
             break
     res = SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs, fro=fro,

@@ -43,8 +43,11 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_THREADS = 192;
-constexpr uint32_t ACC_COLS = 256;   // one 128 x 256 FP32 accumulator
+constexpr int EPI_WARPS = 8;                     // two warps per TMEM lane quarter
+constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
+constexpr uint32_t ACC_COLS = 256;               // one 128 x 256 FP32 accumulator
+constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;     // two chunk buffers
+constexpr int HALF_COLS = BN / 2;                // columns per epilogue thread
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
@@ -74,6 +77,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -187,11 +194,11 @@ template <bool F16>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
           const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-          int nkb, int epi, int64_t np, float* __restrict__ out, uint16_t* __restrict__ out_hi,
-          uint16_t* __restrict__ out_lo, const float* __restrict__ xprev,
-          Part3* __restrict__ part, const Tile* __restrict__ tiles, DevState* st, int step,
+          int nkb, int ch, int epi, int64_t np, float* __restrict__ out,
+          uint16_t* __restrict__ out_hi, uint16_t* __restrict__ out_lo,
+          const float* __restrict__ xprev, Part3* __restrict__ part,
+          const Tile* __restrict__ tiles, DevState* st, int step,
           const float* __restrict__ a_scale, float* __restrict__ zmax) {
-  constexpr uint32_t TMEM_COLS = F16 ? 2 * ACC_COLS : ACC_COLS;
   constexpr uint32_t kIdesc = idesc_for(F16);
   {
     const int m = *((volatile const int*)&st->stop_at);
@@ -202,21 +209,26 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
                                              ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
-  __shared__ double red1[4], red2[4], red3[4];
+  uint64_t* tfull = empty + STAGES;   // [2] chunk accumulated in TMEM buffer b
+  uint64_t* tempty = tfull + 2;       // [2] TMEM buffer b drained by the epilogue warps
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  __shared__ double red1[EPI_WARPS], red2[EPI_WARPS], red3[EPI_WARPS];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Tile t = tiles[blockIdx.x];
   int* abortf = &st->abort_flag;
   const int total_kb = 3 * nkb;
+  const int nchunks = total_kb / ch;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA_hi)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB_hi)) : "memory");
@@ -259,66 +271,90 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      for (int kb = 0; kb < total_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph, abortf)) break;
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        // the epilogue has drained buffer b (chunk c-2)
+        if (!mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, abortf)) break;
         tc_fence_after();
-        const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
-        const uint64_t adesc = sdesc_sw128(a_addr);
-        const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
-        // FP16X2: segment 0 -> accumulator 0, segments 1-2 -> accumulator 1
-        const bool acc1 = F16 && kb >= nkb;
-        const uint32_t dtm = acc1 ? tmem + ACC_COLS : tmem;
-        const int kfirst = acc1 ? nkb : 0;
+        const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
+        for (int kb = c * ch; kb < (c + 1) * ch; ++kb) {
+          const int s = kb % STAGES;
+          const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph, abortf)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t adesc = sdesc_sw128(a_addr);
+          const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
-          umma_bf16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
-                    (kb > kfirst || k > 0) ? 1u : 0u);
+          for (int k = 0; k < BK / 16; ++k) {
+            // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
+            umma_bf16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                      (kb > c * ch || k > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[s]);
         }
-        umma_commit(&empty[s]);
+        umma_commit(&tfull[b]);
       }
-      umma_commit(accf);
     }
   } else {
-    // epilogue warps 2..5
+    // epilogue warps 2 .. 2+EPI_WARPS-1: warp w reads TMEM lanes 32*(w%4) .. +31 and
+    // columns [half*128, half*128+128). Each K chunk is drained from TMEM into
+    // FP32 registers with round-to-nearest adds (FP16X2: chunks of the hi*lo
+    // segments weighted by 2^-11).
+    const int e = warp - 2;
     const int q = warp & 3;
+    const int half = e >> 2;
     const int r = q * 32 + lane;
     const int64_t gi = t.row0 + r;
-    bool ok = mbar_wait(accf, 0, abortf);
-    ok = __all_sync(0xffffffffu, ok);
-    tc_fence_after();
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HALF_COLS);
+    float acc[HALF_COLS];
+#pragma unroll
+    for (int j = 0; j < HALF_COLS; ++j) acc[j] = 0.0f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      bool w = mbar_wait(&tfull[b], (uint32_t)(c >> 1) & 1u, abortf);
+      w = __all_sync(0xffffffffu, w);
+      if (!w) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const float wgt = (F16 && (c * ch) >= nkb) ? (1.0f / kLoScale) : 1.0f;
+#pragma unroll
+      for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(trow + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] = fmaf(wgt, __uint_as_float(v[j]), acc[c0 + j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
     double t1 = 0.0, t2 = 0.0, f = 0.0;
     if (ok && !*((volatile int*)abortf)) {
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
       const int sg = (epi == EPI_SQUARE) ? st->sigma[step] : 1;
       const int64_t bat = gi / np;  // batch entry of this row (stacked A)
       const float inv_s = (F16 && a_scale) ? 1.0f / a_scale[bat] : 1.0f;
       float zm = 0.0f;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+      for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
         float val[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) val[j] = __uint_as_float(v[j]);
-        if (F16) {
-          uint32_t w[16];
-          tmem_ld16(trow + ACC_COLS + (uint32_t)c0, w);
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            val[j] = (val[j] + __uint_as_float(w[j]) * (1.0f / kLoScale)) * inv_s;
-        }
-        const int64_t gj0 = t.col0 + c0;
+        for (int j = 0; j < 16; ++j) val[j] = acc[c0 + j] * inv_s;
+        const int64_t gj0 = t.col0 + half * HALF_COLS + c0;
         if (epi == EPI_PLAIN) {
           float4* dst = reinterpret_cast<float4*>(out + gi * np + gj0);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             dst[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
-          if (zmax) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) zm = fmaxf(zm, fabsf(val[j]));
-          }
+          for (int j = 0; j < 16; ++j) zm = fmaxf(zm, fabsf(val[j]));
           continue;
         }
         if (gj0 + 15 < gi) continue;  // whole chunk below the diagonal
@@ -368,15 +404,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
           const int64_t gj = gj0 + j;
           if (gj < gi) continue;
           const double d = (double)val[j];
-          const double r = (double)res[j];
+          const double rr = (double)res[j];
           if (gj == gi) {
             t1 += d;
             t2 += d * d;
-            f += r * r;
+            f += rr * rr;
           } else {
             store_split<F16>(out, out_hi, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
             t2 += 2.0 * d * d;
-            f += 2.0 * r * r;
+            f += 2.0 * rr * rr;
           }
         }
       }
@@ -393,19 +429,24 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         f += __shfl_xor_sync(0xffffffffu, f, o);
       }
       if (lane == 0) {
-        red1[q] = t1;
-        red2[q] = t2;
-        red3[q] = f;
+        red1[e] = t1;
+        red2[e] = t2;
+        red3[e] = f;
       }
     }
   }
 
   tc_fence_before();
   __syncthreads();
-  if (epi == EPI_SQUARE && threadIdx.x == 0)
-    part[blockIdx.x] = Part3{red1[0] + red1[1] + red1[2] + red1[3],
-                             red2[0] + red2[1] + red2[2] + red2[3],
-                             red3[0] + red3[1] + red3[2] + red3[3]};
+  if (epi == EPI_SQUARE && threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int w = 0; w < EPI_WARPS; ++w) {
+      s1 += red1[w];
+      s2 += red2[w];
+      s3 += red3[w];
+    }
+    part[blockIdx.x] = Part3{s1, s2, s3};
+  }
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -485,14 +526,17 @@ cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t 
     return cudaErrorInvalidValue;
   }
   const int nkb = (int)(np / BK);
+  // K chunk drained from TMEM into FP32 registers: 8 k-blocks (512) when it
+  // divides a segment, else 4 (np is a multiple of 256, so nkb of 4)
+  const int ch = (nkb % 8 == 0) ? 8 : 4;
   if (f16)
     k_gemm_tc<true><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, nkb, epi, np, static_cast<float*>(out.master), out.hi, out.lo,
-        x_prev, part, tiles, st, step, a_scale, zmax);
+        ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
+        out.lo, x_prev, part, tiles, st, step, a_scale, zmax);
   else
     k_gemm_tc<false><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, nkb, epi, np, static_cast<float*>(out.master), out.hi, out.lo,
-        x_prev, part, tiles, st, step, nullptr, nullptr);
+        ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
+        out.lo, x_prev, part, tiles, st, step, nullptr, nullptr);
   return cudaGetLastError();
 }
 

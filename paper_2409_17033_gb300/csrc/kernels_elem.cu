@@ -11,6 +11,7 @@ namespace sp2 {
 namespace {
 
 constexpr int kRedThreads = 256;
+constexpr int kStall = 4;  // steps without a new minimum of f that mark the precision floor
 
 template <typename T>
 __device__ __forceinline__ double ld_as_double(const void* p, int64_t idx) {
@@ -196,10 +197,21 @@ __global__ void k_decide(const Part3* part, DevState* st, DecideParams p) {
     const double e = fabs(t1 - t2);
     bool stop = false;
     if (p.idem_tol > 0.0 && e <= p.idem_tol) stop = true;
-    // precision floor on f: f_{s-2} <= gate and f_s >= f_{s-2}
-    if (!stop && s >= 3 && p.floor_gate > 0.0 && st->f[s - 2] <= p.floor_gate &&
-        st->f[s] >= st->f[s - 2])
-      stop = true;
+    // precision floor on f (see the stop rule in sp2.h):
+    //   opposite branches at steps s-2, s-1, f_{s-2} <= gate and f_s >= f_{s-2}; or
+    //   min f_1..f_{s-STALL} <= gate and none of f_{s-STALL+1..s} below it
+    if (!stop && p.floor_gate > 0.0) {
+      if (s >= 3 && st->sigma[s - 2] != st->sigma[s - 1] && st->f[s - 2] <= p.floor_gate &&
+          st->f[s] >= st->f[s - 2])
+        stop = true;
+      if (!stop && s > kStall) {
+        double best = st->f[1];
+        for (int k = 2; k <= s - kStall; ++k) best = fmin(best, st->f[k]);
+        double recent = st->f[s - kStall + 1];
+        for (int k = s - kStall + 2; k <= s; ++k) recent = fmin(recent, st->f[k]);
+        if (best <= p.floor_gate && recent >= best) stop = true;
+      }
+    }
     if (stop) {
       st->stop_at = s;
       return;

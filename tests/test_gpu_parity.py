@@ -5,8 +5,11 @@ Tolerances (relative Frobenius norm unless stated):
   FP32 mode      D 1e-5, chi / D1 / a1 1e-3 (single-precision products).
   BF16X2 mode    one product against the oracle's emulation of the same split
                  products (Eq. MixPrecMult in FP64): 2e-6 (FP32 accumulation
-                 order only); converged D 1e-4, chi / D1 / a1 1e-2 against the
+                 only); converged D 1e-4, chi / D1 / a1 1e-2 against the
                  exact closed forms (hi+lo carries ~16 significant bits).
+  FP16X2 mode    one product 1e-6 against the emulation; converged D 3e-5,
+                 chi / D1 / a1 1e-3 (hi+lo carries ~22 bits; the tensor-core
+                 accumulation is drained to FP32 registers every K chunk).
 """
 import numpy as np
 import pytest
@@ -207,7 +210,7 @@ def test_split_modes_converged_against_closed_forms(sp2, c1, mode):
     p, _ = c1
     H = cuda(p.H, torch.float32)
     A = cuda(p.A[None], torch.float32)
-    tolD, tolC = (1e-4, 1e-2) if mode == "bf16x2" else (1e-5, 1e-3)
+    tolD, tolC = (1e-4, 1e-2) if mode == "bf16x2" else (3e-5, 1e-3)
     chi_b, D, info = sp2.sp2_susceptibility(H, p.nocc, A, "backward", mode=mode, want_density=True)
     chi_f, _, _ = sp2.sp2_susceptibility(H, p.nocc, A, "forward", mode=mode)
     assert info["converged"]
@@ -249,7 +252,7 @@ def test_ragged_sizes(sp2, n, mode):
     chi, D, info = sp2.sp2_susceptibility(cuda(p.H, dt), p.nocc, cuda(p.A[None], dt), "backward",
                                           mode=mode, want_density=True,
                                           idem_tol=1e-10 if mode == "fp64" else 0.0)
-    tolD, tolC = {"fp64": (1e-10, 1e-8), "bf16x2": (1e-4, 1e-2), "fp16x2": (1e-5, 1e-3)}[mode]
+    tolD, tolC = {"fp64": (1e-10, 1e-8), "bf16x2": (1e-4, 1e-2), "fp16x2": (3e-5, 1e-3)}[mode]
     assert rel(host(D), exact.density_zero_T(p.e, p.Q, p.nocc)) < tolD
     chi_ex = exact.response_zero_T(p.e, p.Q, p.nocc, p.A)
     if np.linalg.norm(chi_ex) > 0:

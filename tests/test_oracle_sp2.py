@@ -103,17 +103,18 @@ def test_floor_rule_in_emulated_split_precision():
     emin, emax = sp2.gershgorin_bounds(tb.H)
     a, b = sp2.sp2_scaling(emin, emax)
     X = (a * np.eye(512) + b * tb.H).astype(np.float32).astype(np.float64)
-    fro, errs = [], [sp2.traces(X)[0] - sp2.traces(X)[1]]
+    fro, errs, sig = [], [sp2.traces(X)[0] - sp2.traces(X)[1]], []
     M = None
     for n in range(1, 100):
         t1, t2 = sp2.traces(X)
         s = sp2.choose_sigma(t1, t2, tb.nocc)
+        sig.append(s)
         X2 = split.mixed_product(X, X, "bf16")
         fro.append(sp2.idem_fro(X, X2))
         X = (X2 if s > 0 else 2 * X - X2).astype(np.float32).astype(np.float64)
         t1, t2 = sp2.traces(X)
         errs.append(t1 - t2)
-        if sp2.stop_now(n, errs, fro, 0.0, 0.03, 4):
+        if sp2.stop_now(n, errs, fro, sig, 0.0, 0.03, 4):
             M = n
             break
     assert M is not None
