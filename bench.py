@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--ckpt-k", type=int, default=4)
-    ap.add_argument("--mode", default="bf16x2")
+    ap.add_argument("--mode", default="fp16x2")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -276,7 +276,7 @@ def run_ours(args, ws, rank):
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x2 (split bf16 products, f32 accumulate/master)",
+        "vs_baseline": None, "dtype": f"{args.mode} (split 16-bit products, f32 accumulate/master)",
         "data": "synthetic",
         "config": {
             "workload": (f"tight-binding N={n} ({n // 4} sites x 4 orbitals, density 0.1, r<6), "
@@ -290,7 +290,7 @@ def run_ours(args, ws, rank):
         "tc_peak_frac_executed": exec_tflops / peak,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_gemm_tc (tcgen05 split-BF16 product)",
+                     "kernel": "k_gemm_tc (tcgen05 split 16-bit product)",
                      "launches_per_step": prod_launch,
                      "peak_kind": f"bf16_tflops_sustained ({pk_kind})"},
         "quality": quality,
