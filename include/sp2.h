@@ -189,6 +189,31 @@ int sp2_release_history(sp2_handle_t h);
 int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, int64_t K,
                       int64_t N, int dtype, int q_diag_only, double* out);
 
+/* response_contract_noalloc: the same contraction as response_contract for
+ * callers that cannot allocate device memory -- code whose device memory is
+ * owned entirely by another allocator, or which must not pay for the device
+ * synchronisation that cudaMalloc/cudaFree can imply -- and that therefore
+ * cannot create a handle. The paper has no counterpart to this entry point.
+ *
+ * Nothing is allocated or freed by any call: the reduction partials live in
+ * one file-scope device array of 2^17 doubles (1 MiB), which every GPU that
+ * loads libsp2.so holds until the process exits. The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it; make that first call before any stream
+ * capture begins. P, Q and out must be device memory (host pointers are
+ * rejected); out[l*K + k] = sum_ij P_l[i,j] Q_k[i,j] as in response_contract.
+ * The work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream) and the call returns without waiting: out is valid once
+ * the stream has reached it. All calls share the one partial-sum array,
+ * which keeps the last call's contents; every partial a call reads is written
+ * by that same call first, so nothing needs clearing, but calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array
+ * and must be ordered by the caller.
+ * Returns SP2_EINVAL for negative sizes, a bad dtype, null or host pointers,
+ * or L * K > 65535; SP2_ECUDA if a CUDA call fails. */
+int response_contract_noalloc(const void* P, int64_t L, const void* Q, int64_t K, int64_t N,
+                              int dtype, int q_diag_only, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

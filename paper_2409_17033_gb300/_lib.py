@@ -108,6 +108,9 @@ EXPORTS = {
     "sp2_release_history": (C.c_int, [C.c_void_p]),
     "response_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "response_contract_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                            C.c_int64, C.c_int, C.c_int, C.c_void_p,
+                                            C.c_void_p]),
 }
 
 _lib = None
