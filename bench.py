@@ -94,17 +94,22 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_per_launch(n: int):
-    """DRAM bytes per product launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def traffic_per_launch(n: int, m: int, k: int):
+    """DRAM bytes per product launch from the committed ncu capture, averaged
+    over this solve's launch mix (M + M - ceil(M/k) squares, M response
+    products), if the capture was taken on the current kernel source and at
+    this size; else None."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     try:
         d = json.load(open(TRAFFIC_FILE))
         src = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
-        if d.get("kernel_sha256") != src:
+        if d.get("kernel_sha256") != src or int(d.get("n", -1)) != n:
             return None
-        return float(d["bytes_per_launch_at_n"][str(n)])
+        sq = d["square"]["read_bytes"] + d["square"]["write_bytes"]
+        pl = d["plain"]["read_bytes"] + d["plain"]["write_bytes"]
+        nsq = m + (m - (m + k - 1) // k)
+        return (nsq * sq + m * pl) / (nsq + m)
     except Exception:
         return None
 
@@ -266,7 +271,7 @@ def run_ours(args, ws, rank):
     alg = statistics.mean(i["algorithmic_flops"] for i in infos)
     achieved = alg / (prod_ms * 1e-3) / 1e12
     peak = pk["bf16_tflops_sustained"]
-    traffic = traffic_per_launch(n)
+    traffic = traffic_per_launch(n, info["M"], args.ckpt_k)
     gpu_launches = sum(i["kernel_launches"] for i in infos)
 
     quality = {

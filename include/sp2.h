@@ -182,6 +182,32 @@ int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad,
 /* Release a kept X_n history (device memory) without destroying the handle. */
 int sp2_release_history(sp2_handle_t h);
 
+/* Finite electronic temperature (Sec. V.B): the Fermi-Dirac density matrix
+ *     D = f(H) = (exp((H - mu I) / kT) + I)^(-1)
+ * and the first-order responses D1_k = d f(H + lambda B_k) / d lambda, which
+ * are the finite-temperature susceptibilities chi^A when B_k = A (Eq.
+ * Suscept_Der). canonical != 0 adds the chemical-potential response mu_1
+ * chosen so that Tr[D1_k] = 0 (the mu_1 rule stated with Eq. CP_SCF);
+ * canonical = 0 gives the grand-canonical response at fixed mu.
+ *
+ * The paper cites the recursion without printing it; the one implemented is
+ * the odds-squaring recursion f(2x) = f(x)^2 / (f(x)^2 + (1 - f(x))^2), written
+ * for delta = f - 1/2:
+ *     delta_0 = -(1 / (kT 2^(n+2))) (H - mu I),
+ *     delta_{j+1} = 2 delta_j (I + 4 delta_j^2)^(-1),  j < n,   D = I/2 + delta_n,
+ * with n = n_doublings, the inverse by Newton-Schulz iterations whose count
+ * follows from a spectral bound of delta_j, and the responses by the chain
+ * rule of each step over the stored delta_j. The result is the Fermi
+ * function of H up to a log-odds error of 2 (x/2)^3 / (3 4^n), x = (e - mu)/kT.
+ * Requires |e - mu| / (kT 2^(n+2)) < 1/2 over the Gershgorin bounds of H
+ * (SP2_EINVAL otherwise: raise n_doublings).
+ * H: N x N. B: K x N x N, or K x N diagonals when b_diag_only != 0; K = 0 is
+ * allowed. opts->mode selects the arithmetic (all four modes). D (nullable):
+ * N x N. D1: K x N x N. info->M = n_doublings. */
+int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, double kT,
+              const void* B, int64_t K, int b_diag_only, int canonical, int n_doublings,
+              const sp2_opts* opts, void* D, void* D1, sp2_info* info);
+
 /* out[l*K + k] = sum_ij P_l[i,j] * Q_k[i,j] (= Tr[P_l Q_k] for symmetric P_l or Q_k),
  * accumulated in FP64. P: L x N x N. Q: K x N x N, or K x N diagonals when
  * q_diag_only != 0 (then out = sum_i P_l[i,i] Q_k[i]). out: L*K doubles

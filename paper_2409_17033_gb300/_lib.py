@@ -106,6 +106,9 @@ EXPORTS = {
     "sp2_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                               C.POINTER(Info)]),
     "sp2_release_history": (C.c_int, [C.c_void_p]),
+    "sp2_fermi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double,
+                            C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.POINTER(Opts),
+                            C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "response_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "response_contract_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,

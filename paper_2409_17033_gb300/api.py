@@ -11,6 +11,7 @@ Functions (see include/sp2.h for the exact semantics):
   sp2_response(H, nocc, H1, ...)                Eq. DMPert (DM1)      -> (D1, D, info)
   sp2_susceptibility(H, nocc, A, direction=...) Eq. DMSuscept / DM2   -> (chi, D, info)
   sp2_adjoint(G, handle)                        Eq. DM2 on kept X_n   -> grad
+  sp2_fermi(H, mu, kT, B, ...)                  Sec. V.B finite T     -> (D1, D, info)
   response_contract(P, Q, diag_only=...)        Tr[P_l Q_k]           -> (L, K) float64
 """
 from __future__ import annotations
@@ -23,7 +24,7 @@ import torch
 from . import _lib as L
 
 __all__ = ["Handle", "make_opts", "sp2_density", "sp2_response", "sp2_susceptibility",
-           "sp2_adjoint", "response_contract", "SP2Error"]
+           "sp2_adjoint", "sp2_fermi", "response_contract", "SP2Error"]
 
 SP2Error = L.SP2Error
 
@@ -204,6 +205,27 @@ def sp2_adjoint(G, handle: Handle):
     rc = h.lib.sp2_adjoint(h.h, _ptr(G), n, _dtype_code(G), _ptr(out), C.byref(info))
     h.check(rc)
     return out
+
+
+def sp2_fermi(H, mu: float, kT: float, B=None, diag_only: bool = False, canonical: bool = True,
+              n_doublings: int = 20, mode="fp64", want_density: bool = True,
+              handle: Handle | None = None, **kw):
+    """Finite-temperature density f(H) and first-order responses to B_k
+    (Sec. V.B; canonical: Tr[D1_k] = 0). B: (K, N, N) or (K, N) diagonals.
+    Returns (D1 or None, D or None, info)."""
+    h = handle or default_handle()
+    h.bind_stream()
+    n = H.shape[0]
+    k = 0 if B is None else B.shape[0]
+    D1 = _empty_like(H, (k, n, n)) if k else None
+    D = _empty_like(H, (n, n)) if want_density else None
+    opts, _keep = make_opts(mode, **kw)
+    info = L.Info()
+    rc = h.lib.sp2_fermi(h.h, _ptr(H), n, _dtype_code(H), float(mu), float(kT),
+                         _ptr(B) if k else None, k, 1 if diag_only else 0, 1 if canonical else 0,
+                         int(n_doublings), C.byref(opts), _ptr(D), _ptr(D1), C.byref(info))
+    h.check(rc)
+    return D1, D, info.to_dict()
 
 
 def response_contract(P, Q, diag_only: bool = False, handle: Handle | None = None):

@@ -198,7 +198,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
           uint16_t* __restrict__ out_hi, uint16_t* __restrict__ out_lo,
           const float* __restrict__ xprev, Part3* __restrict__ part,
           const Tile* __restrict__ tiles, DevState* st, int step,
-          const float* __restrict__ a_scale, float* __restrict__ zmax) {
+          const float* __restrict__ a_scale, const float* __restrict__ b_scale,
+          float* __restrict__ zmax) {
   constexpr uint32_t kIdesc = idesc_for(F16);
   {
     const int m = *((volatile const int*)&st->stop_at);
@@ -340,7 +341,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
     if (ok && !*((volatile int*)abortf)) {
       const int sg = (epi == EPI_SQUARE) ? st->sigma[step] : 1;
       const int64_t bat = gi / np;  // batch entry of this row (stacked A)
-      const float inv_s = (F16 && a_scale) ? 1.0f / a_scale[bat] : 1.0f;
+      float inv_s = (F16 && a_scale) ? 1.0f / a_scale[bat] : 1.0f;
+      if (F16 && b_scale) inv_s /= b_scale[0];
       float zm = 0.0f;
 #pragma unroll
       for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
@@ -499,7 +501,7 @@ void tc_tile_shape(int* bm, int* bn) {
 cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
                            const float* x_prev, Part3* part, const Tile* tiles, int ntiles,
                            DevState* st, int step, const float* a_scale, float* zmax,
-                           cudaStream_t s, char* errbuf, size_t errlen) {
+                           cudaStream_t s, char* errbuf, size_t errlen, const float* b_scale) {
   if (ntiles <= 0) return cudaSuccess;
   const bool f16 = mode == SP2_MODE_FP16X2;
   static bool attr_done[2] = {false, false};
@@ -532,11 +534,11 @@ cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t 
   if (f16)
     k_gemm_tc<true><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
         ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
-        out.lo, x_prev, part, tiles, st, step, a_scale, zmax);
+        out.lo, x_prev, part, tiles, st, step, a_scale, b_scale, zmax);
   else
     k_gemm_tc<false><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
         ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
-        out.lo, x_prev, part, tiles, st, step, nullptr, nullptr);
+        out.lo, x_prev, part, tiles, st, step, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -664,6 +664,109 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
   return SP2_OK;
 }
 
+
+// --------------------------------------------------------------- finite temperature
+// A padded matrix of the finite-temperature recursion with its plane scale
+// (FP16X2: a power of two from its max; 1 otherwise) and max accumulator.
+struct FMat {
+  MatBuf m;
+  float* scale = nullptr;  // device float (FP16X2)
+  float* amax = nullptr;   // device float (FP16X2)
+};
+
+int fmat(sp2_handle_t h, const std::string& name, int64_t np, int mode, FMat* f) {
+  TRY(mat(h, name, np, np, mode, &f->m));
+  if (mode == SP2_MODE_FP16X2) {
+    void* p;
+    TRY(ws(h, name + ".s", 2 * sizeof(float), &p));
+    f->scale = static_cast<float*>(p);
+    f->amax = f->scale + 1;
+  }
+  return SP2_OK;
+}
+
+// hi/lo planes of f from its master (FP16X2: scale from f->amax)
+int fplanes(Ctx& c, FMat& f) {
+  sp2_handle_t h = c.h;
+  if (c.mode == SP2_MODE_BF16X2) {
+    CK(launch_split(f.m, c.np, c.np, c.mode, h->stream));
+    c.kernels++;
+  } else if (c.mode == SP2_MODE_FP16X2) {
+    ScaleBuf sc;
+    sc.ymax = f.amax;
+    sc.yscale = f.scale;
+    sc.B = 1;
+    CK(launch_split_scaled(f.m, c.np, sc, 0, h->stream));
+    c.kernels += 2;
+  }
+  return SP2_OK;
+}
+
+// C = L R for symmetric R (R's rows are the K-major operand); master only,
+// plus C's max in FP16X2 (planes follow from fplanes when C is an operand)
+int fprod(Ctx& c, FMat& C, const FMat& L, const FMat& R) {
+  sp2_handle_t h = c.h;
+  const Tile* tl;
+  int nt;
+  TRY(tile_list(h, c.mode, c.np, c.np, false, &tl, &nt));
+  int bm, bn;
+  tile_shape(c.mode, &bm, &bn);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.timing) {
+    TRY(ev_pair(c, &e0, &e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  if (split_mode(c.mode)) {
+    const bool f16 = c.mode == SP2_MODE_FP16X2;
+    if (f16) CK(cudaMemsetAsync(C.amax, 0, sizeof(float), h->stream));
+    char eb[256] = {0};
+    TcOperand a{L.m.hi, L.m.lo, c.np}, b{R.m.hi, R.m.lo, c.np};
+    cudaError_t e = launch_gemm_tc(c.mode, EPI_PLAIN, a, b, c.np, C.m, nullptr, c.part, tl, nt,
+                                   c.st, 0, f16 ? L.scale : nullptr, f16 ? C.amax : nullptr,
+                                   h->stream, eb, sizeof eb, f16 ? R.scale : nullptr);
+    if (e != cudaSuccess) return fail(h, SP2_ECUDA, "finite-T product: %s %s", cudaGetErrorString(e), eb);
+  } else {
+    CK(launch_gemm_simt(c.mode, EPI_PLAIN, L.m.master, c.np, R.m.master, c.np, C.m.master, nullptr,
+                        c.part, tl, nt, c.st, 0, h->stream));
+  }
+  if (c.timing) {
+    CK(cudaEventRecord(e1, h->stream));
+    c.timed.push_back({0, 0});
+  }
+  c.launches++;
+  c.kernels++;
+  c.flops += 2.0 * bm * bn * (double)c.np * k_mult(c.mode) * nt;
+  c.alg += 2.0 * (double)c.n * (double)c.n * (double)c.n * k_mult(c.mode);
+  return SP2_OK;
+}
+
+// out = z1 (Z1 + Z1^T) + z2 (Z2 + Z2^T) + a A + id I, then planes when `planes`
+int fcomb(Ctx& c, FMat& out, const FMat* Z1, double z1, const FMat* Z2, double z2,
+          const FMat* A, double a, double id, bool planes) {
+  sp2_handle_t h = c.h;
+  const bool f16 = c.mode == SP2_MODE_FP16X2;
+  if (f16) CK(cudaMemsetAsync(out.amax, 0, sizeof(float), h->stream));
+  CK(launch_combine(c.mode, out.m.master, c.np, c.n, Z1 ? Z1->m.master : nullptr, z1,
+                    Z2 ? Z2->m.master : nullptr, z2, A ? A->m.master : nullptr, a, id,
+                    f16 ? out.amax : nullptr, h->stream));
+  c.kernels++;
+  if (planes) TRY(fplanes(c, out));
+  return SP2_OK;
+}
+
+// Newton-Schulz iterations for Z = S^{-1} with spec(S) in [1, 1 + 4 b^2]:
+// Z_0 = 2 / (2 + 4 b^2) I, error ratio r = 4 b^2 / (2 + 4 b^2) squared each
+// iteration; enough iterations for r^(2^k) <= tol.
+int ns_iterations(double b, double tol) {
+  const double r = 4.0 * b * b / (2.0 + 4.0 * b * b);
+  int k = 0;
+  double e = r;
+  while (e > tol && k < 12) {
+    e = e * e;
+    ++k;
+  }
+  return k;
+}
 }  // namespace
 
 // ====================================================================== C ABI
@@ -918,6 +1021,203 @@ int sp2_release_history(sp2_handle_t h) {
     if (kv.first.rfind("ckpt.", 0) == 0 || kv.first.rfind("seg.", 0) == 0) names.push_back(kv.first);
   cudaStreamSynchronize(h->stream);
   for (auto& nm : names) ws_free(h, nm);
+  return SP2_OK;
+}
+
+
+int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, double kT,
+              const void* B, int64_t K, int b_diag_only, int canonical, int n_doublings,
+              const sp2_opts* opts_in, void* D, void* D1, sp2_info* info) {
+  if (!h) return SP2_EINVAL;
+  if (N < 0 || K < 0) return fail(h, SP2_EINVAL, "negative size");
+  if (dtype != SP2_F64 && dtype != SP2_F32) return fail(h, SP2_EINVAL, "unknown dtype %d", dtype);
+  if (!(kT > 0.0) || !std::isfinite(mu)) return fail(h, SP2_EINVAL, "kT must be > 0, mu finite");
+  if (n_doublings < 1 || n_doublings > 64) return fail(h, SP2_EINVAL, "n_doublings outside 1..64");
+  if (N > 0 && (!H || (K > 0 && (!B || !D1)))) return fail(h, SP2_EINVAL, "null pointer");
+  sp2_opts o = resolve(opts_in);
+  TRY(validate_opts(h, &o));
+  if (info) memset(info, 0, sizeof *info);
+  if (N == 0) {
+    if (info) info->converged = 1;
+    return SP2_OK;
+  }
+  const int mode = o.mode;
+  const int64_t np = pad_n(N);
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const void *Hd, *Bd = nullptr;
+  TRY(stage_in(h, "H", H, mb, &Hd));
+  if (K > 0) TRY(stage_in(h, "B", B, (size_t)K * (b_diag_only ? N : N * N) * dsize(dtype), &Bd));
+  OutStage od, oy;
+  if (D) TRY(stage_out(h, "D", D, mb, &od));
+  if (K > 0) TRY(stage_out(h, "Y", D1, (size_t)K * mb, &oy));
+  Ctx c;
+  TRY(make_ctx(h, mode, N, np, o.time_kernels != 0, &c));
+  CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));  // never halted
+
+  // spectral bound of H - mu I (Gershgorin, Sec. II estimates)
+  const int nb = bounds_nparts(N);
+  void* bp;
+  TRY(ws(h, "bounds.part", nb * sizeof(double2), &bp));
+  CK(launch_bounds(Hd, N, dtype, static_cast<double2*>(bp), nb, h->d_state, h->stream));
+  c.kernels += 2;
+  TRY(poll_state(h));
+  const double emin = h->h_state->bounds[0], emax = h->h_state->bounds[1];
+  if (!std::isfinite(emin) || !std::isfinite(emax))
+    return fail(h, SP2_ENONFINITE, "non-finite spectral bounds (NaN/Inf in H)");
+  const double cst = 1.0 / (kT * std::ldexp(1.0, n_doublings + 2));
+  double b = cst * std::fmax(std::fabs(emax - mu), std::fabs(emin - mu));
+  if (!(b < 0.5))
+    return fail(h, SP2_EINVAL, "n_doublings = %d too small: |e - mu| / (kT 2^(n+2)) reaches %g >= 1/2",
+                n_doublings, b);
+  const double tol = mode == SP2_MODE_FP64 ? 1e-17 : 1e-8;
+  const int n = n_doublings;
+
+  // forward pass: store delta_j and W_j, j = 0..n-1
+  std::vector<FMat> dl(n + 1), W(n);
+  for (int j = 0; j <= n; ++j) TRY(fmat(h, "ft.d" + std::to_string(j), np, mode, &dl[j]));
+  for (int j = 0; j < n; ++j) TRY(fmat(h, "ft.W" + std::to_string(j), np, mode, &W[j]));
+  FMat P, S, T, U, Z2[2];
+  TRY(fmat(h, "ft.P", np, mode, &P));
+  TRY(fmat(h, "ft.S", np, mode, &S));
+  TRY(fmat(h, "ft.T", np, mode, &T));
+  TRY(fmat(h, "ft.U", np, mode, &U));
+  TRY(fmat(h, "ft.Z0", np, mode, &Z2[0]));
+  TRY(fmat(h, "ft.Z1", np, mode, &Z2[1]));
+  // delta_0 = c mu I - c H (planes with scale 1: |delta| < 1/2)
+  CK(launch_init(Hd, N, np, 1, dtype, 0, 0, cst * mu, -cst, mode, dl[0].m, nullptr, 0, nullptr,
+                 h->stream));
+  c.kernels++;
+  if (mode == SP2_MODE_FP16X2) {
+    const float one = 1.0f;
+    CK(cudaMemcpyAsync(dl[0].scale, &one, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  for (int j = 0; j < n; ++j) {
+    // S = I + 4 delta^2, symmetrised: I + 2 (P + P^T)
+    TRY(fprod(c, P, dl[j], dl[j]));
+    TRY(fcomb(c, S, &P, 2.0, nullptr, 0.0, nullptr, 0.0, 1.0, true));
+    // W = S^{-1} by Newton-Schulz: Z <- 2 Z - sym(Z (S Z))
+    const int kns = ns_iterations(b, tol);
+    const double z0 = 2.0 / (2.0 + 4.0 * b * b);
+    int zi = 0;
+    FMat* Zc = (kns == 0) ? &W[j] : &Z2[0];
+    TRY(fcomb(c, *Zc, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, z0, true));
+    for (int it = 0; it < kns; ++it) {
+      FMat& Zin = *Zc;
+      FMat& Zout = (it == kns - 1) ? W[j] : Z2[1 - zi];
+      TRY(fprod(c, T, S, Zin));
+      TRY(fplanes(c, T));
+      TRY(fprod(c, U, Zin, T));
+      TRY(fcomb(c, Zout, &U, -0.5, nullptr, 0.0, &Zin, 2.0, 0.0, true));
+      zi = 1 - zi;
+      Zc = &Zout;
+    }
+    // delta_{j+1} = 2 delta W, symmetrised: V + V^T with V = delta W
+    TRY(fprod(c, P, dl[j], W[j]));
+    TRY(fcomb(c, dl[j + 1], &P, 1.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+    b = 2.0 * b / (1.0 + 4.0 * b * b);
+  }
+  // D = I/2 + delta_n
+  if (D) {
+    TRY(fcomb(c, P, nullptr, 0.0, nullptr, 0.0, &dl[n], 1.0, 0.5, false));
+    CK(launch_copy_out(P.m, N, np, 1, mode, 1.0, od.dev, dtype, h->stream));
+    c.kernels++;
+    TRY(finish_out(h, od));
+  }
+
+  // responses (each perturbation through the stored history); canonical adds
+  // the response to I, and D1_k -= (Tr D1_k / Tr R_I) R_I
+  if (K > 0) {
+    FMat dd[2], E, F1, dW, G1, RI;
+    TRY(fmat(h, "ft.dd0", np, mode, &dd[0]));
+    TRY(fmat(h, "ft.dd1", np, mode, &dd[1]));
+    TRY(fmat(h, "ft.E", np, mode, &E));
+    TRY(fmat(h, "ft.F1", np, mode, &F1));
+    TRY(fmat(h, "ft.dW", np, mode, &dW));
+    TRY(fmat(h, "ft.G1", np, mode, &G1));
+    if (canonical) TRY(fmat(h, "ft.RI", np, mode, &RI));
+    void* ones = nullptr;
+    if (canonical) {
+      TRY(ws(h, "ft.ones", (size_t)N * dsize(dtype), &ones));
+      std::vector<double> h1(N, 1.0);
+      std::vector<float> h1f(N, 1.0f);
+      CK(cudaMemcpyAsync(ones, dtype == SP2_F64 ? (const void*)h1.data() : (const void*)h1f.data(),
+                         (size_t)N * dsize(dtype), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    void* trp;
+    TRY(ws(h, "ft.tr", 2 * sizeof(double), &trp));
+    double* tr = static_cast<double*>(trp);
+    const int64_t per = b_diag_only ? N : N * N;
+    const int64_t total = K + (canonical ? 1 : 0);
+    double trI = 0.0;
+    for (int64_t kk = total - 1; kk >= 0; --kk) {  // the response to I first (canonical)
+      const bool isI = canonical && kk == K;
+      const void* src = isI ? ones : static_cast<const char*>(Bd) + (size_t)kk * per * dsize(dtype);
+      const int diag = isI ? 1 : b_diag_only;
+      int cur = 0;
+      FMat& d0 = dd[0];
+      if (mode == SP2_MODE_FP16X2) CK(cudaMemsetAsync(d0.amax, 0, sizeof(float), h->stream));
+      CK(launch_init(src, N, np, 1, dtype, diag, 0, 0.0, -cst, mode, d0.m, nullptr, 0,
+                     mode == SP2_MODE_FP16X2 ? d0.amax : nullptr, h->stream));
+      c.kernels++;
+      if (mode == SP2_MODE_FP16X2) TRY(fplanes(c, d0));
+      for (int j = 0; j < n; ++j) {
+        FMat& din = dd[cur];
+        FMat& dout = (j == n - 1 && isI) ? RI : dd[1 - cur];
+        // E = d delta delta + delta d delta = Z1 + Z1^T, Z1 = d delta * delta
+        TRY(fprod(c, P, din, dl[j]));
+        TRY(fcomb(c, E, &P, 1.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+        // dW = -4 W E W = -2 (F2 + F2^T), F2 = (W E) W
+        TRY(fprod(c, F1, W[j], E));
+        TRY(fplanes(c, F1));
+        TRY(fprod(c, U, F1, W[j]));
+        TRY(fcomb(c, dW, &U, -2.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+        // d delta' = 2 (d delta W + delta dW) = (G1 + G1^T) + (G2 + G2^T)
+        TRY(fprod(c, G1, din, W[j]));
+        TRY(fprod(c, T, dl[j], dW));
+        TRY(fcomb(c, dout, &G1, 1.0, &T, 1.0, nullptr, 0.0, 0.0, j < n - 1));
+        cur = 1 - cur;
+      }
+      if (isI) {
+        CK(launch_trace(mode, RI.m.master, np, N, tr + 1, h->stream));
+        CK(cudaMemcpyAsync(&h->h_state->bounds[1], tr + 1, sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        trI = h->h_state->bounds[1];
+        c.kernels++;
+        continue;
+      }
+      FMat& res = dd[cur];
+      FMat* outm = &res;
+      if (canonical) {
+        CK(launch_trace(mode, res.m.master, np, N, tr, h->stream));
+        CK(cudaMemcpyAsync(&h->h_state->bounds[0], tr, sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const double trk = h->h_state->bounds[0];
+        c.kernels++;
+        // res - (trk / trI) RI, written as (a/2)(RI + RI^T) + res (RI is exactly symmetric)
+        TRY(fcomb(c, G1, &RI, -0.5 * trk / trI, nullptr, 0.0, &res, 1.0, 0.0, false));
+        outm = &G1;
+      }
+      CK(launch_copy_out(outm->m, N, np, 1, mode, 1.0,
+                         static_cast<char*>(oy.dev) + (size_t)kk * N * N * dsize(dtype), dtype,
+                         h->stream));
+      c.kernels++;
+    }
+    TRY(finish_out(h, oy));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) {
+    info->M = n;
+    info->converged = 1;
+    info->alpha = 0.5;
+    info->beta = -cst;
+    info->eps_min = emin;
+    info->eps_max = emax;
+  }
+  fill_timing(c, 1 << 30, info);
   return SP2_OK;
 }
 

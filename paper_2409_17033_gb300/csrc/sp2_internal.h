@@ -164,11 +164,24 @@ struct TcOperand {   // hi/lo planes of a stacked operand, rows x np
   int64_t rows;
 };
 // a_scale (FP16X2, EPI_PLAIN): per batch entry of A, the plane scale to divide
-// out; zmax (FP16X2, EPI_PLAIN): per batch entry, receives max |Z|.
+// out; b_scale (FP16X2, nullable): the plane scale of B; zmax (FP16X2,
+// EPI_PLAIN): per batch entry, receives max |Z|.
 cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
                            const float* x_prev, Part3* part, const Tile* tiles, int ntiles,
                            DevState* st, int step, const float* a_scale, float* zmax,
-                           cudaStream_t s, char* errbuf, size_t errlen);
+                           cudaStream_t s, char* errbuf, size_t errlen,
+                           const float* b_scale = nullptr);
 void tc_tile_shape(int* bm, int* bn);
+
+// finite temperature (fermi_kernels.cu)
+// out = z1 (Z1 + Z1^T) + z2 (Z2 + Z2^T) + a A + id I on the padded np x np
+// matrices (null operands skipped, I only on the caller's n x n block);
+// amax (nullable) receives max |out| (must start at 0).
+cudaError_t launch_combine(int mode, void* out, int64_t np, int64_t n, const void* Z1, double z1,
+                           const void* Z2, double z2, const void* A, double a, double id,
+                           float* amax, cudaStream_t s);
+// out[0] = Tr of the caller's n x n block, FP64
+cudaError_t launch_trace(int mode, const void* M, int64_t np, int64_t n, double* out,
+                         cudaStream_t s);
 
 }  // namespace sp2
