@@ -208,6 +208,61 @@ int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, do
               const void* B, int64_t K, int b_diag_only, int canonical, int n_doublings,
               const sp2_opts* opts, void* D, void* D1, sp2_info* info);
 
+/* Self-consistent first-order response (Appendix, Eq. DM_CP_SCF; its dual is
+ * Eq. CP_SCF) with a site-charge interaction: for each of F external site
+ * potentials V_ext (F x n_sites), find site charges q with
+ *     q = q_out(q),  q_out(q) = site charges of D1[H1 = diag(u (x) 1_norb)],
+ *     u = V_ext + K q  (K: n_sites x n_sites),  q_a = sum_{mu in site a} D1_{mu mu},
+ * D1 being the zero-temperature response of Eq. DM1 (merged form, Eq. DMPert)
+ * to the site-diagonal perturbation u. N = n_sites * norb; orbitals of site a
+ * are a*norb .. a*norb+norb-1.
+ * Mixers: linear (the paper's constant c_mix = alpha), Anderson over the last
+ * `history` iterates (the "more advanced SCF acceleration" the Appendix
+ * mentions), or a learned correction to linear mixing,
+ * q <- q + alpha r + ||r|| MLP(r / ||r||), r = q_out - q, with
+ * y = W2 relu(W1 x) (no biases; W1: hidden x n_sites, W2: n_sites x hidden,
+ * device FP32; bf16_infer rounds weights and activations to bfloat16).
+ * The residual judging convergence is the plain method's:
+ * ||q_out(q) - q||_2 / ||q_out(0)||_2 over all fields, stopping at <= tol.
+ * K, V_ext and q (F x n_sites out, the last iterate) are double, device or
+ * host. residuals: host array of max_iter doubles (nullable); iterations:
+ * host int. traj_r / traj_q (nullable, device doubles of max_iter x F x
+ * n_sites): residual and iterate of every iteration (training data). */
+typedef enum { SP2_MIX_LINEAR = 0, SP2_MIX_ANDERSON = 1, SP2_MIX_MLP = 2 } sp2_mixer;
+
+typedef struct {
+  int mixer;            /* sp2_mixer */
+  double alpha;         /* linear mixing parameter; Anderson's damping of the residual */
+  int history;          /* Anderson history length (1..32) */
+  double tol;           /* relative residual tolerance */
+  int max_iter;         /* SCF iteration cap */
+  const float* W1;      /* MLP weights (device) for SP2_MIX_MLP */
+  const float* W2;
+  int hidden;           /* MLP width */
+  int bf16_infer;       /* 1: bfloat16 operands in inference */
+} sp2_scf_opts;
+
+int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc, int norb,
+                     const double* Ksite, const double* Vext, int64_t F, const sp2_scf_opts* so,
+                     const sp2_opts* opts, double* q, double* residuals, int* iterations,
+                     double* traj_r, double* traj_q, sp2_info* info);
+
+/* Learned preconditioner kernels (FP32 training, bf16 or FP32 inference).
+ * The map is y = W2 relu(W1 x) for x of length d_in, W1: d_h x d_in,
+ * W2: d_in x d_h, all row-major device FP32; X, T, Y are P x d_in.
+ * The paper has no learned part; these serve the SCF mixer above. */
+int sp2_mlp_forward(sp2_handle_t h, const float* W1, const float* W2, int d_in, int d_h,
+                    const float* X, int64_t P, float* Y, int bf16);
+/* Mean squared error L = sum (Y - T)^2 / P and its gradients dW1, dW2
+ * (device FP32); *loss is a host double. */
+int sp2_mlp_loss_grad(sp2_handle_t h, const float* W1, const float* W2, int d_in, int d_h,
+                      const float* X, const float* T, int64_t P, double* loss, float* dW1,
+                      float* dW2);
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8) on (X, T),
+ * updating W1, W2 in place; loss_hist (host, nullable) gets each step's loss. */
+int sp2_mlp_train(sp2_handle_t h, float* W1, float* W2, int d_in, int d_h, const float* X,
+                  const float* T, int64_t P, int steps, double lr, double* loss_hist);
+
 /* out[l*K + k] = sum_ij P_l[i,j] * Q_k[i,j] (= Tr[P_l Q_k] for symmetric P_l or Q_k),
  * accumulated in FP64. P: L x N x N. Q: K x N x N, or K x N diagonals when
  * q_diag_only != 0 (then out = sum_i P_l[i,i] Q_k[i]). out: L*K doubles

@@ -28,4 +28,4 @@ Parity status: every function here is pinned by a `-m "not gpu"` test against
 a closed form, an invariant, brute force or a library routine (see
 ``tests/test_oracle_*.py``). None is marked "parity unpinned".
 """
-from . import exact, sp2, split  # noqa: F401
+from . import exact, fermi, scf, sp2, split  # noqa: F401

@@ -88,6 +88,22 @@ class Info(C.Structure):
         }
 
 
+class ScfOpts(C.Structure):
+    _fields_ = [
+        ("mixer", C.c_int),
+        ("alpha", C.c_double),
+        ("history", C.c_int),
+        ("tol", C.c_double),
+        ("max_iter", C.c_int),
+        ("W1", C.c_void_p),
+        ("W2", C.c_void_p),
+        ("hidden", C.c_int),
+        ("bf16_infer", C.c_int),
+    ]
+
+
+MIXERS = {"linear": 0, "anderson": 1, "mlp": 2}
+
 EXPORTS = {
     "sp2_default_opts": (None, [C.POINTER(Opts)]),
     "sp2_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_size_t]),
@@ -111,6 +127,17 @@ EXPORTS = {
                             C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "response_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "sp2_scf_response": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_int,
+                                   C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(ScfOpts),
+                                   C.POINTER(Opts), C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.POINTER(Info)]),
+    "sp2_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                  C.c_int64, C.c_void_p, C.c_int]),
+    "sp2_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                                    C.c_void_p, C.c_void_p]),
+    "sp2_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_void_p]),
     "response_contract_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                             C.c_int64, C.c_int, C.c_int, C.c_void_p,
                                             C.c_void_p]),

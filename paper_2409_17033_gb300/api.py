@@ -12,6 +12,8 @@ Functions (see include/sp2.h for the exact semantics):
   sp2_susceptibility(H, nocc, A, direction=...) Eq. DMSuscept / DM2   -> (chi, D, info)
   sp2_adjoint(G, handle)                        Eq. DM2 on kept X_n   -> grad
   sp2_fermi(H, mu, kT, B, ...)                  Sec. V.B finite T     -> (D1, D, info)
+  sp2_scf_response(H, nocc, norb, K, Vext, ...) Eq. DM_CP_SCF         -> (q, residuals, iters, traj)
+  mlp_forward / mlp_loss_grad / mlp_train       learned SCF preconditioner
   response_contract(P, Q, diag_only=...)        Tr[P_l Q_k]           -> (L, K) float64
 """
 from __future__ import annotations
@@ -24,7 +26,8 @@ import torch
 from . import _lib as L
 
 __all__ = ["Handle", "make_opts", "sp2_density", "sp2_response", "sp2_susceptibility",
-           "sp2_adjoint", "sp2_fermi", "response_contract", "SP2Error"]
+           "sp2_adjoint", "sp2_fermi", "sp2_scf_response", "mlp_forward", "mlp_loss_grad",
+           "mlp_train", "response_contract", "SP2Error"]
 
 SP2Error = L.SP2Error
 
@@ -226,6 +229,78 @@ def sp2_fermi(H, mu: float, kT: float, B=None, diag_only: bool = False, canonica
                          int(n_doublings), C.byref(opts), _ptr(D), _ptr(D1), C.byref(info))
     h.check(rc)
     return D1, D, info.to_dict()
+
+
+def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
+                     alpha: float = 0.3, history: int = 8, tol: float = 1e-6, max_iter: int = 100,
+                     W1=None, W2=None, bf16_infer: bool = True, record: bool = False,
+                     mode="fp64", handle: Handle | None = None, allow_noconv: bool = False, **kw):
+    """Self-consistent site-charge response for F fields (rows of Vext, float64).
+    K: (n_sites, n_sites) float64. Returns (q, residuals, iterations, (traj_r,
+    traj_q) or None); q and the trajectories live where Vext lives."""
+    h = handle or default_handle()
+    h.bind_stream()
+    n = H.shape[0]
+    F, ns = Vext.shape
+    so = L.ScfOpts()
+    so.mixer = L.MIXERS[mixer]
+    so.alpha = float(alpha)
+    so.history = int(history)
+    so.tol = float(tol)
+    so.max_iter = int(max_iter)
+    so.W1 = _ptr(W1) if W1 is not None else None
+    so.W2 = _ptr(W2) if W2 is not None else None
+    so.hidden = int(W1.shape[0]) if W1 is not None else 0
+    so.bf16_infer = 1 if bf16_infer else 0
+    q = _empty_like(Vext, (F, ns))
+    res = np.zeros(max_iter, dtype=np.float64)
+    its = C.c_int(0)
+    tr = tq = None
+    if record:
+        dev = Vext.device if isinstance(Vext, torch.Tensor) else "cuda"
+        tr = torch.zeros((max_iter, F, ns), dtype=torch.float64, device=dev)
+        tq = torch.zeros((max_iter, F, ns), dtype=torch.float64, device=dev)
+    opts, _keep = make_opts(mode, **kw)
+    info = L.Info()
+    rc = h.lib.sp2_scf_response(h.h, _ptr(H), n, _dtype_code(H), float(nocc), int(norb), _ptr(K),
+                                _ptr(Vext), F, C.byref(so), C.byref(opts), _ptr(q),
+                                res.ctypes.data, C.byref(its), _ptr(tr) if record else None,
+                                _ptr(tq) if record else None, C.byref(info))
+    h.check(rc, allow_noconv)
+    k = its.value
+    return q, res[:k], k, ((tr[:k], tq[:k]) if record else None)
+
+
+def mlp_forward(W1, W2, X, bf16: bool = False, handle: Handle | None = None):
+    """Y = relu(X W1^T) W2^T (device float32 tensors)."""
+    h = handle or default_handle()
+    h.bind_stream()
+    Y = torch.empty((X.shape[0], W2.shape[0]), dtype=torch.float32, device=X.device)
+    h.check(h.lib.sp2_mlp_forward(h.h, _ptr(W1), _ptr(W2), W1.shape[1], W1.shape[0], _ptr(X),
+                                  X.shape[0], _ptr(Y), 1 if bf16 else 0))
+    return Y
+
+
+def mlp_loss_grad(W1, W2, X, T, handle: Handle | None = None):
+    """(loss, dW1, dW2) of the mean squared error sum (Y - T)^2 / P."""
+    h = handle or default_handle()
+    h.bind_stream()
+    g1 = torch.empty_like(W1)
+    g2 = torch.empty_like(W2)
+    loss = C.c_double(0.0)
+    h.check(h.lib.sp2_mlp_loss_grad(h.h, _ptr(W1), _ptr(W2), W1.shape[1], W1.shape[0], _ptr(X),
+                                    _ptr(T), X.shape[0], C.byref(loss), _ptr(g1), _ptr(g2)))
+    return loss.value, g1, g2
+
+
+def mlp_train(W1, W2, X, T, steps: int, lr: float, handle: Handle | None = None):
+    """`steps` full-batch Adam steps in place; returns the loss history."""
+    h = handle or default_handle()
+    h.bind_stream()
+    hist = np.zeros(max(steps, 1), dtype=np.float64)
+    h.check(h.lib.sp2_mlp_train(h.h, _ptr(W1), _ptr(W2), W1.shape[1], W1.shape[0], _ptr(X),
+                                _ptr(T), X.shape[0], int(steps), float(lr), hist.ctypes.data))
+    return hist[:steps]
 
 
 def response_contract(P, Q, diag_only: bool = False, handle: Handle | None = None):

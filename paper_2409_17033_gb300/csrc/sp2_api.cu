@@ -1253,3 +1253,291 @@ int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- SCF response + MLP
+namespace {
+
+// Solve the (m+1) x (m+1) Anderson system [G 1; 1^T 0] [c; lam] = [0; 1]
+// by Gaussian elimination with partial pivoting (host, tiny). G gets a
+// relative Tikhonov shift for rank-deficient histories.
+void anderson_coeffs(const double* G, int m, double* c) {
+  double A[33][34];
+  double tr = 0.0;
+  for (int i = 0; i < m; ++i) tr += G[i * m + i];
+  const double shift = 1e-12 * (tr > 0 ? tr / m : 1.0);
+  for (int i = 0; i <= m; ++i)
+    for (int j = 0; j <= m + 1; ++j) A[i][j] = 0.0;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i][j] = G[i * m + j];
+    A[i][i] += shift;
+    A[i][m] = 1.0;
+    A[m][i] = 1.0;
+  }
+  A[m][m + 1] = 1.0;
+  const int n = m + 1;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i][k]) > std::fabs(A[p][k])) p = i;
+    if (p != k)
+      for (int j = 0; j <= n; ++j) std::swap(A[k][j], A[p][j]);
+    const double d = A[k][k];
+    if (d == 0.0) continue;
+    for (int i = k + 1; i < n; ++i) {
+      const double f = A[i][k] / d;
+      for (int j = k; j <= n; ++j) A[i][j] -= f * A[k][j];
+    }
+  }
+  double x[33];
+  for (int i = n - 1; i >= 0; --i) {
+    double s = A[i][n];
+    for (int j = i + 1; j < n; ++j) s -= A[i][j] * x[j];
+    x[i] = A[i][i] != 0.0 ? s / A[i][i] : 0.0;
+  }
+  for (int i = 0; i < m; ++i) c[i] = x[i];
+}
+
+// MLP forward for a batch: Hr = relu(X W1^T) (P x dh), Y = Hr W2^T (P x din)
+int mlp_fwd(sp2_handle_t h, const float* W1, const float* W2, int din, int dh, const float* X,
+            int64_t P, float* Hr, float* Y, int bf16) {
+  CK(launch_sgemm(P, dh, din, 1.0f, X, din, 0, W1, din, 1, 0.0f, Hr, dh, 1, bf16, h->stream));
+  CK(launch_sgemm(P, din, dh, 1.0f, Hr, dh, 0, W2, dh, 1, 0.0f, Y, din, 0, bf16, h->stream));
+  return SP2_OK;
+}
+
+// loss and gradients (backpropagation through y = W2 relu(W1 x)); loss on device
+int mlp_grad(sp2_handle_t h, const float* W1, const float* W2, int din, int dh, const float* X,
+             const float* T, int64_t P, double* dloss, float* dW1, float* dW2, float* Hr, float* Y,
+             float* dY, float* dH) {
+  TRY(mlp_fwd(h, W1, W2, din, dh, X, P, Hr, Y, 0));
+  CK(cudaMemsetAsync(dloss, 0, sizeof(double), h->stream));
+  CK(launch_mse_grad(Y, T, P * din, 1.0f / (float)P, dY, dloss, h->stream));
+  // dW2 = dY^T Hr (din x dh); dH = dY W2 (P x dh) masked; dW1 = dH^T X (dh x din)
+  CK(launch_sgemm(din, dh, P, 1.0f, dY, din, 1, Hr, dh, 0, 0.0f, dW2, dh, 0, 0, h->stream));
+  CK(launch_sgemm(P, dh, din, 1.0f, dY, din, 0, W2, dh, 0, 0.0f, dH, dh, 0, 0, h->stream));
+  CK(launch_relu_mask(dH, Hr, P * dh, h->stream));
+  CK(launch_sgemm(dh, din, P, 1.0f, dH, dh, 1, X, din, 0, 0.0f, dW1, din, 0, 0, h->stream));
+  return SP2_OK;
+}
+
+int mlp_scratch(sp2_handle_t h, int din, int dh, int64_t P, float** Hr, float** Y, float** dY,
+                float** dH) {
+  void *a, *b, *c2, *d;
+  TRY(ws(h, "mlp.H", (size_t)P * dh * sizeof(float), &a));
+  TRY(ws(h, "mlp.Y", (size_t)P * din * sizeof(float), &b));
+  TRY(ws(h, "mlp.dY", (size_t)P * din * sizeof(float), &c2));
+  TRY(ws(h, "mlp.dH", (size_t)P * dh * sizeof(float), &d));
+  *Hr = static_cast<float*>(a);
+  *Y = static_cast<float*>(b);
+  *dY = static_cast<float*>(c2);
+  *dH = static_cast<float*>(d);
+  return SP2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sp2_mlp_forward(sp2_handle_t h, const float* W1, const float* W2, int din, int dh,
+                    const float* X, int64_t P, float* Y, int bf16) {
+  if (!h) return SP2_EINVAL;
+  if (din <= 0 || dh <= 0 || P < 0) return fail(h, SP2_EINVAL, "bad MLP sizes");
+  if (P == 0) return SP2_OK;
+  if (!W1 || !W2 || !X || !Y) return fail(h, SP2_EINVAL, "null pointer");
+  void* a;
+  TRY(ws(h, "mlp.H", (size_t)P * dh * sizeof(float), &a));
+  TRY(mlp_fwd(h, W1, W2, din, dh, X, P, static_cast<float*>(a), Y, bf16));
+  CK(cudaStreamSynchronize(h->stream));
+  return SP2_OK;
+}
+
+int sp2_mlp_loss_grad(sp2_handle_t h, const float* W1, const float* W2, int din, int dh,
+                      const float* X, const float* T, int64_t P, double* loss, float* dW1,
+                      float* dW2) {
+  if (!h) return SP2_EINVAL;
+  if (din <= 0 || dh <= 0 || P <= 0) return fail(h, SP2_EINVAL, "bad MLP sizes");
+  if (!W1 || !W2 || !X || !T || !dW1 || !dW2 || !loss) return fail(h, SP2_EINVAL, "null pointer");
+  float *Hr, *Y, *dY, *dH;
+  TRY(mlp_scratch(h, din, dh, P, &Hr, &Y, &dY, &dH));
+  void* dl;
+  TRY(ws(h, "mlp.loss", sizeof(double), &dl));
+  TRY(mlp_grad(h, W1, W2, din, dh, X, T, P, static_cast<double*>(dl), dW1, dW2, Hr, Y, dY, dH));
+  CK(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SP2_OK;
+}
+
+int sp2_mlp_train(sp2_handle_t h, float* W1, float* W2, int din, int dh, const float* X,
+                  const float* T, int64_t P, int steps, double lr, double* loss_hist) {
+  if (!h) return SP2_EINVAL;
+  if (din <= 0 || dh <= 0 || P <= 0 || steps < 0) return fail(h, SP2_EINVAL, "bad MLP sizes");
+  if (!W1 || !W2 || !X || !T) return fail(h, SP2_EINVAL, "null pointer");
+  float *Hr, *Y, *dY, *dH;
+  TRY(mlp_scratch(h, din, dh, P, &Hr, &Y, &dY, &dH));
+  const int64_t n1 = (int64_t)dh * din, n2 = (int64_t)din * dh;
+  void *g, *mv, *dl;
+  TRY(ws(h, "mlp.g", (size_t)(n1 + n2) * sizeof(float), &g));
+  TRY(ws(h, "mlp.mv", (size_t)2 * (n1 + n2) * sizeof(float), &mv));
+  TRY(ws(h, "mlp.lossv", (size_t)(steps > 0 ? steps : 1) * sizeof(double), &dl));
+  float* g1 = static_cast<float*>(g);
+  float* g2 = g1 + n1;
+  float* m1 = static_cast<float*>(mv);
+  float* v1 = m1 + n1;
+  float* m2 = v1 + n1;
+  float* v2 = m2 + n2;
+  CK(cudaMemsetAsync(mv, 0, (size_t)2 * (n1 + n2) * sizeof(float), h->stream));
+  double* dloss = static_cast<double*>(dl);
+  for (int t = 1; t <= steps; ++t) {
+    TRY(mlp_grad(h, W1, W2, din, dh, X, T, P, dloss + (t - 1), g1, g2, Hr, Y, dY, dH));
+    CK(launch_adam(W1, g1, m1, v1, n1, (float)lr, 0.9f, 0.999f, 1e-8f, t, h->stream));
+    CK(launch_adam(W2, g2, m2, v2, n2, (float)lr, 0.9f, 0.999f, 1e-8f, t, h->stream));
+  }
+  if (loss_hist && steps > 0)
+    CK(cudaMemcpyAsync(loss_hist, dloss, (size_t)steps * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SP2_OK;
+}
+
+int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc, int norb,
+                     const double* Ksite, const double* Vext, int64_t F, const sp2_scf_opts* so,
+                     const sp2_opts* opts_in, double* q_out, double* residuals, int* iterations,
+                     double* traj_r, double* traj_q, sp2_info* info) {
+  TRY(check_common(h, H, N, dtype, nocc));
+  if (!so) return fail(h, SP2_EINVAL, "null sp2_scf_opts");
+  if (norb < 1 || N % norb != 0) return fail(h, SP2_EINVAL, "N must be a multiple of norb");
+  if (F < 1 || !Ksite || !Vext || !q_out) return fail(h, SP2_EINVAL, "bad SCF arguments");
+  if (so->max_iter < 1) return fail(h, SP2_EINVAL, "max_iter < 1");
+  if (so->mixer == SP2_MIX_ANDERSON && (so->history < 1 || so->history > 32))
+    return fail(h, SP2_EINVAL, "Anderson history outside 1..32");
+  if (so->mixer == SP2_MIX_MLP && (!so->W1 || !so->W2 || so->hidden < 1))
+    return fail(h, SP2_EINVAL, "MLP mixer needs W1, W2 and hidden");
+  if (so->mixer < 0 || so->mixer > 2) return fail(h, SP2_EINVAL, "unknown mixer");
+  sp2_opts o = resolve(opts_in);
+  TRY(validate_opts(h, &o));
+  if (info) memset(info, 0, sizeof *info);
+  const int64_t ns = N / norb, np = pad_n(N), tot = F * ns;
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const void *Hd, *Kd, *Vd;
+  TRY(stage_in(h, "H", H, mb, &Hd));
+  TRY(stage_in(h, "scf.K", Ksite, (size_t)ns * ns * sizeof(double), &Kd));
+  TRY(stage_in(h, "scf.V", Vext, (size_t)tot * sizeof(double), &Vd));
+  OutStage oq;
+  TRY(stage_out(h, "scf.qout", q_out, (size_t)tot * sizeof(double), &oq));
+  void *pq, *pqo, *pr, *pu, *pub, *pn;
+  TRY(ws(h, "scf.q", tot * sizeof(double), &pq));
+  TRY(ws(h, "scf.qo", tot * sizeof(double), &pqo));
+  TRY(ws(h, "scf.r", tot * sizeof(double), &pr));
+  TRY(ws(h, "scf.u", tot * sizeof(double), &pu));
+  TRY(ws(h, "scf.ub", (size_t)F * N * dsize(dtype), &pub));
+  TRY(ws(h, "scf.norms", 2 * sizeof(double), &pn));
+  double *q = static_cast<double*>(pq), *qo = static_cast<double*>(pqo), *r = static_cast<double*>(pr);
+  double* u = static_cast<double*>(pu);
+  double* norms = static_cast<double*>(pn);
+  const int m = so->mixer == SP2_MIX_ANDERSON ? so->history : 0;
+  double *Qh = nullptr, *Rh = nullptr, *G = nullptr, *cf = nullptr;
+  if (m > 0) {
+    void *a, *b, *c2, *d;
+    TRY(ws(h, "scf.Qh", (size_t)m * tot * sizeof(double), &a));
+    TRY(ws(h, "scf.Rh", (size_t)m * tot * sizeof(double), &b));
+    TRY(ws(h, "scf.G", (size_t)F * m * m * sizeof(double), &c2));
+    TRY(ws(h, "scf.c", (size_t)F * m * sizeof(double), &d));
+    Qh = static_cast<double*>(a);
+    Rh = static_cast<double*>(b);
+    G = static_cast<double*>(c2);
+    cf = static_cast<double*>(d);
+  }
+  float *mx = nullptr, *my = nullptr, *mh = nullptr;
+  double* nr = nullptr;
+  if (so->mixer == SP2_MIX_MLP) {
+    void *a, *b, *c2, *d;
+    TRY(ws(h, "scf.mx", tot * sizeof(float), &a));
+    TRY(ws(h, "scf.my", tot * sizeof(float), &b));
+    TRY(ws(h, "scf.mh", (size_t)F * so->hidden * sizeof(float), &c2));
+    TRY(ws(h, "scf.nr", F * sizeof(double), &d));
+    mx = static_cast<float*>(a);
+    my = static_cast<float*>(b);
+    mh = static_cast<float*>(c2);
+    nr = static_cast<double*>(d);
+  }
+  CK(cudaMemsetAsync(q, 0, tot * sizeof(double), h->stream));
+  Ctx c;
+  TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
+  MatBuf X[2], Y[2];
+  double norm0 = 0.0;
+  int it = 0;
+  bool done = false;
+  std::vector<double> Gh, ch;
+  for (; it < so->max_iter && !done; ++it) {
+    // u = V + K q, perturbation diag(u (x) 1_norb), response, site charges
+    CK(launch_site_potential(static_cast<const double*>(Vd), static_cast<const double*>(Kd), q, F,
+                             ns, u, h->stream));
+    CK(launch_expand_sites(u, F, ns, norb, pub, dtype, h->stream));
+    c.kernels += 2;
+    Sp2Out rr;
+    TRY(run_sp2(h, Hd, N, dtype, nocc, o, pub, F, 1, false, X, Y, c, &rr));
+    if (!rr.converged) return fail(h, SP2_ENOCONV, "SP2 did not converge inside the SCF loop");
+    CK(launch_site_charges(Y[rr.yslot].master, o.mode, F, ns, norb, np, qo, h->stream));
+    CK(cudaMemsetAsync(norms, 0, 2 * sizeof(double), h->stream));
+    CK(launch_residual(qo, q, tot, r, norms, h->stream));
+    c.kernels += 2;
+    if (traj_r) CK(cudaMemcpyAsync(traj_r + (size_t)it * tot, r, tot * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, h->stream));
+    if (traj_q) CK(cudaMemcpyAsync(traj_q + (size_t)it * tot, q, tot * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->h_state->bounds, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double s1 = h->h_state->bounds[0], s2 = h->h_state->bounds[1];
+    if (it == 0) norm0 = std::sqrt(s2);
+    const double res = norm0 > 0.0 ? std::sqrt(s1) / norm0 : std::sqrt(s1);
+    if (residuals) residuals[it] = res;
+    if (!std::isfinite(res)) return fail(h, SP2_ENONFINITE, "non-finite SCF residual");
+    if (res <= so->tol) {
+      done = true;
+      break;
+    }
+    if (so->mixer == SP2_MIX_LINEAR) {
+      CK(launch_axpy_d(q, so->alpha, r, tot, h->stream));
+      c.kernels++;
+    } else if (so->mixer == SP2_MIX_ANDERSON) {
+      const int slot = it % m, me = it + 1 < m ? it + 1 : m;
+      CK(cudaMemcpyAsync(Qh + (size_t)slot * tot, q, tot * sizeof(double), cudaMemcpyDeviceToDevice,
+                         h->stream));
+      CK(cudaMemcpyAsync(Rh + (size_t)slot * tot, r, tot * sizeof(double), cudaMemcpyDeviceToDevice,
+                         h->stream));
+      CK(launch_gram(Rh, me, F, ns, tot, G, h->stream));
+      Gh.resize((size_t)F * me * me);
+      ch.resize((size_t)F * me);
+      CK(cudaMemcpyAsync(Gh.data(), G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int64_t f = 0; f < F; ++f) anderson_coeffs(&Gh[(size_t)f * me * me], me, &ch[(size_t)f * me]);
+      CK(cudaMemcpyAsync(cf, ch.data(), ch.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         h->stream));
+      CK(launch_anderson_combine(Qh, Rh, cf, me, F, ns, tot, so->alpha, q, h->stream));
+      CK(cudaStreamSynchronize(h->stream));  // ch is reused next iteration
+      c.kernels += 2;
+    } else {
+      // q <- q + alpha r + ||r|| MLP(r / ||r||): a learned correction to linear mixing
+      CK(launch_normalise_rows(r, F, ns, mx, nr, h->stream));
+      TRY(mlp_fwd(h, so->W1, so->W2, (int)ns, so->hidden, mx, F, mh, my, so->bf16_infer));
+      CK(launch_axpy_d(q, so->alpha, r, tot, h->stream));
+      CK(launch_apply_update(q, my, nr, F, ns, h->stream));
+      c.kernels += 5;
+    }
+  }
+  if (iterations) *iterations = done ? it + 1 : it;
+  CK(cudaMemcpyAsync(oq.dev, q, tot * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  TRY(finish_out(h, oq));
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) {
+    info->converged = done ? 1 : 0;
+    info->M = 0;
+  }
+  fill_timing(c, 1 << 30, info);
+  if (!done) return fail(h, SP2_ENOCONV, "SCF residual above tol after %d iterations", so->max_iter);
+  return SP2_OK;
+}
+
+}  // extern "C"

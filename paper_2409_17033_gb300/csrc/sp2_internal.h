@@ -184,4 +184,32 @@ cudaError_t launch_combine(int mode, void* out, int64_t np, int64_t n, const voi
 cudaError_t launch_trace(int mode, const void* M, int64_t np, int64_t n, double* out,
                          cudaStream_t s);
 
+// self-consistent response and MLP (scf_kernels.cu)
+cudaError_t launch_sgemm(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                         int ta, const float* B, int64_t ldb, int tb, float beta, float* C,
+                         int64_t ldc, int relu, int bf16, cudaStream_t s);
+cudaError_t launch_site_potential(const double* V, const double* K, const double* q, int64_t F,
+                                  int64_t ns, double* u, cudaStream_t s);
+cudaError_t launch_expand_sites(const double* u, int64_t F, int64_t ns, int norb, void* out,
+                                int dtype, cudaStream_t s);
+cudaError_t launch_site_charges(const void* Y, int mode, int64_t F, int64_t ns, int norb,
+                                int64_t np, double* q, cudaStream_t s);
+cudaError_t launch_residual(const double* qout, const double* q, int64_t total, double* r,
+                            double* out2, cudaStream_t s);
+cudaError_t launch_axpy_d(double* y, double a, const double* x, int64_t total, cudaStream_t s);
+cudaError_t launch_gram(const double* R, int m, int64_t F, int64_t ns, int64_t stride, double* G,
+                        cudaStream_t s);
+cudaError_t launch_anderson_combine(const double* Qh, const double* Rh, const double* c, int m,
+                                    int64_t F, int64_t ns, int64_t stride, double alpha, double* q,
+                                    cudaStream_t s);
+cudaError_t launch_normalise_rows(const double* r, int64_t F, int64_t ns, float* x, double* nr,
+                                  cudaStream_t s);
+cudaError_t launch_apply_update(double* q, const float* y, const double* nr, int64_t F, int64_t ns,
+                                cudaStream_t s);
+cudaError_t launch_mse_grad(const float* Y, const float* T, int64_t total, float scale, float* dY,
+                            double* loss, cudaStream_t s);
+cudaError_t launch_relu_mask(float* dH, const float* Hr, int64_t total, cudaStream_t s);
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t total, float lr,
+                        float b1, float b2, float eps, int t, cudaStream_t s);
+
 }  // namespace sp2

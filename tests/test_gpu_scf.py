@@ -1,0 +1,144 @@
+"""Self-consistent response (Eq. DM_CP_SCF with a site-charge G) and the MLP
+preconditioner kernels on the GPU, against the FP64 oracle.
+
+Tolerances: FP64 response path 1e-8 for the SCF solution and its residual
+history; the MLP kernels run in FP32: loss and gradients 1e-5 relative to
+the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import exact, scf
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2409_17033_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def small():
+    tb = workloads.tight_binding(256, seed=0)
+    e, V = exact.eigh(tb.H)
+    chi0 = scf.chi0_sites(e, V, tb.nocc, tb.norb)
+    K = workloads.site_kernel(tb, "regularised")
+    Vx = workloads.site_fields(tb, 6, seed=3)
+    return tb, chi0, K, Vx
+
+
+@pytest.mark.parametrize("mixer", ["linear", "anderson"])
+def test_scf_fp64_matches_oracle(pkg, small, mixer):
+    tb, chi0, K, Vx = small
+    H = torch.from_numpy(tb.H).cuda()
+    q, res, its, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, Vx, mixer=mixer, alpha=0.3, history=8,
+                                          tol=1e-9, max_iter=300, mode="fp64", idem_tol=1e-13)
+    q_or, res_or = scf.scf_iterate(chi0, K, Vx, mixer=mixer, alpha=0.3, hist=8, tol=1e-9,
+                                   max_iter=300)
+    assert rel(q, scf.scf_exact(chi0, K, Vx)) < 1e-7
+    assert abs(its - len(res_or)) <= 1
+    k = min(its, len(res_or))
+    # Anderson's coefficients amplify rounding differences late in the run
+    assert np.allclose(res[:k], res_or[:k], rtol=1e-6 if mixer == "linear" else 1e-3, atol=1e-10)
+
+
+def test_scf_split_precision(pkg, small):
+    tb, chi0, K, Vx = small
+    H = torch.from_numpy(tb.H).float().cuda()
+    q, res, its, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, Vx, mixer="anderson", tol=1e-5,
+                                          max_iter=200, mode="fp16x2")
+    assert res[-1] <= 1e-5
+    assert rel(q, scf.scf_exact(chi0, K, Vx)) < 1e-3
+
+
+def test_mlp_kernels_against_oracle(pkg):
+    rng = np.random.default_rng(0)
+    din, dh, P = 96, 40, 70
+    W1 = rng.standard_normal((dh, din)) / np.sqrt(din)
+    W2 = rng.standard_normal((din, dh)) / np.sqrt(dh)
+    X = rng.standard_normal((P, din))
+    T = rng.standard_normal((P, din))
+    f = lambda a: torch.from_numpy(a.astype(np.float32)).cuda()  # noqa: E731
+    Y = pkg.mlp_forward(f(W1), f(W2), f(X)).cpu().numpy()
+    W1f, W2f, Xf, Tf = (a.astype(np.float32).astype(np.float64) for a in (W1, W2, X, T))
+    assert rel(Y, scf.mlp_forward(W1f, W2f, Xf)) < 1e-5
+    L, g1, g2 = pkg.mlp_loss_grad(f(W1), f(W2), f(X), f(T))
+    Lr, g1r, g2r = scf.mlp_loss_grad(W1f, W2f, Xf, Tf)
+    assert L == pytest.approx(Lr, rel=1e-5)
+    assert rel(g1.cpu().numpy(), g1r) < 1e-5
+    assert rel(g2.cpu().numpy(), g2r) < 1e-5
+    Yb = pkg.mlp_forward(f(W1), f(W2), f(X), bf16=True).cpu().numpy()
+    assert 1e-5 < rel(Yb, Y) < 2e-2          # bf16 operands: visibly rounded, still close
+
+
+def test_mlp_training_matches_oracle_adam(pkg):
+    """Five full-batch Adam steps on the GPU track the FP64 oracle's."""
+    rng = np.random.default_rng(1)
+    din, dh, P = 32, 16, 50
+    W1 = rng.standard_normal((dh, din)) / np.sqrt(din)
+    W2 = rng.standard_normal((din, dh)) / np.sqrt(dh)
+    X = rng.standard_normal((P, din))
+    T = X @ rng.standard_normal((din, din)).T * 0.3
+    f = lambda a: torch.from_numpy(a.astype(np.float32)).cuda()  # noqa: E731
+    W1g, W2g = f(W1), f(W2)
+    hist = pkg.mlp_train(W1g, W2g, f(X), f(T), steps=5, lr=1e-2)
+    w1, w2 = (a.astype(np.float32).astype(np.float64) for a in (W1, W2))
+    Xf, Tf = (a.astype(np.float32).astype(np.float64) for a in (X, T))
+    m1 = v1 = np.zeros_like(w1)
+    m2 = v2 = np.zeros_like(w2)
+    ref = []
+    for t in range(1, 6):
+        L, g1, g2 = scf.mlp_loss_grad(w1, w2, Xf, Tf)
+        ref.append(L)
+        w1, m1, v1 = scf.adam_step(w1, g1, m1, v1, t, 1e-2)
+        w2, m2, v2 = scf.adam_step(w2, g2, m2, v2, t, 1e-2)
+    assert np.allclose(hist, ref, rtol=1e-4)
+    assert rel(W1g.cpu().numpy(), w1) < 1e-4
+    assert rel(W2g.cpu().numpy(), w2) < 1e-4
+
+
+def test_learned_preconditioner_reduces_iterations(pkg, small):
+    """Train the MLP on residual -> (q* - q - alpha r) pairs from linear-mixing
+    runs of training fields, then precondition held-out fields: fewer SCF
+    iterations than linear mixing to the same residual (judged by the plain
+    method)."""
+    tb, chi0, K, _ = small
+    H = torch.from_numpy(tb.H).cuda()
+    train = workloads.site_fields(tb, 96, seed=10)
+    test = workloads.site_fields(tb, 4, seed=11)
+    tol = 1e-6
+    q_star, _, _, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, train, mixer="anderson", tol=1e-10,
+                                           max_iter=300, mode="fp64")
+    _, _, its, (tr, tq) = pkg.sp2_scf_response(H, tb.nocc, 4, K, train, mixer="linear", alpha=0.3,
+                                               tol=tol, max_iter=300, record=True, mode="fp64")
+    R = tr.reshape(-1, tr.shape[-1]).cpu().numpy()
+    Tt = (torch.from_numpy(q_star).cuda()[None] - tq - 0.3 * tr).reshape(-1, tq.shape[-1]).cpu().numpy()
+    nr = np.linalg.norm(R, axis=1, keepdims=True)
+    keep = nr[:, 0] > 0
+    Xn, Tn = R[keep] / nr[keep], Tt[keep] / nr[keep]
+    ns, dh = Xn.shape[1], 128     # width 2 n_sites: room for a full-rank linear map
+    rng = np.random.default_rng(5)
+    W1 = torch.from_numpy((rng.standard_normal((dh, ns)) / np.sqrt(ns)).astype(np.float32)).cuda()
+    W2 = torch.from_numpy((0.1 * rng.standard_normal((ns, dh)) / np.sqrt(dh)).astype(np.float32)).cuda()
+    f = lambda a: torch.from_numpy(a.astype(np.float32)).cuda()  # noqa: E731
+    hist = pkg.mlp_train(W1, W2, f(Xn), f(Tn), steps=1500, lr=3e-3)
+    assert hist[-1] < 0.2 * hist[0]
+    _, res_lin, it_lin, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, test, mixer="linear", alpha=0.3,
+                                                 tol=tol, max_iter=300, mode="fp64")
+    q_mlp, res_mlp, it_mlp, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, test, mixer="mlp", W1=W1,
+                                                     W2=W2, bf16_infer=True, tol=tol,
+                                                     max_iter=300, mode="fp64")
+    assert res_mlp[-1] <= tol
+    assert it_mlp < it_lin
+    assert rel(q_mlp, scf.scf_exact(chi0, K, test)) < 1e-4

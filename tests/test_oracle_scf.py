@@ -1,0 +1,94 @@
+"""Pins for the self-consistent response oracle and its MLP (CPU only)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import exact, scf
+
+
+@pytest.fixture(scope="module")
+def small():
+    tb = workloads.tight_binding(256, seed=0)          # 64 sites x 4 orbitals
+    e, V = exact.eigh(tb.H)
+    chi0 = scf.chi0_sites(e, V, tb.nocc, tb.norb)
+    K = workloads.site_kernel(tb, "regularised")
+    Vx = workloads.site_fields(tb, 6, seed=3)
+    return tb, e, V, chi0, K, Vx
+
+
+def test_chi0_matches_finite_differences(small):
+    """chi0_ab = d q_a / d u_b against central differences of the projector."""
+    tb, e, V, chi0, K, Vx = small
+    h = 1e-5
+    for b in (0, 17):
+        P = np.zeros(tb.n)
+        P[b * 4:(b + 1) * 4] = 1.0
+        ep, Vp = exact.eigh(tb.H + h * np.diag(P))
+        em, Vm = exact.eigh(tb.H - h * np.diag(P))
+        dD = (exact.density_zero_T(ep, Vp, tb.nocc) - exact.density_zero_T(em, Vm, tb.nocc)) / (2 * h)
+        col = np.diag(dD).reshape(-1, 4).sum(axis=1)
+        assert np.allclose(chi0[:, b], col, rtol=1e-6, atol=1e-9)
+
+
+def test_chi0_symmetric_and_charge_conserving(small):
+    """chi0 is symmetric (Eq. Equivalence for site perturbations) and a
+    uniform potential moves no charge at fixed N_occ (rows sum to zero)."""
+    tb, e, V, chi0, K, Vx = small
+    assert np.allclose(chi0, chi0.T, atol=1e-12)
+    assert np.allclose(chi0.sum(axis=1), 0.0, atol=1e-10)
+
+
+def test_scf_solution_is_fixed_point(small):
+    tb, e, V, chi0, K, Vx = small
+    qs = scf.scf_exact(chi0, K, Vx)
+    qout = (chi0 @ (Vx + qs @ K.T).T).T
+    assert np.linalg.norm(qout - qs) < 1e-10 * max(1.0, np.linalg.norm(qs))
+
+
+@pytest.mark.parametrize("mixer", ["linear", "anderson"])
+def test_mixers_converge_to_exact_solution(small, mixer):
+    tb, e, V, chi0, K, Vx = small
+    q, res = scf.scf_iterate(chi0, K, Vx, mixer=mixer, alpha=0.3, tol=1e-10, max_iter=500)
+    assert res[-1] <= 1e-10
+    assert np.linalg.norm(q - scf.scf_exact(chi0, K, Vx)) < 1e-8 * np.linalg.norm(q)
+
+
+def test_anderson_beats_linear(small):
+    tb, e, V, chi0, K, Vx = small
+    _, rl = scf.scf_iterate(chi0, K, Vx, mixer="linear", tol=1e-8, max_iter=500)
+    _, ra = scf.scf_iterate(chi0, K, Vx, mixer="anderson", tol=1e-8, max_iter=500)
+    assert len(ra) < len(rl)
+
+
+def test_mlp_gradients_by_finite_differences():
+    rng = np.random.default_rng(0)
+    W1 = rng.standard_normal((7, 5)) * 0.5
+    W2 = rng.standard_normal((5, 7)) * 0.5
+    X = rng.standard_normal((9, 5))
+    T = rng.standard_normal((9, 5))
+    L, g1, g2 = scf.mlp_loss_grad(W1, W2, X, T)
+    h = 1e-6
+    for W, g in ((W1, g1), (W2, g2)):
+        for idx in [(0, 0), (3, 2), (4, 4)]:
+            Wp = W.copy(); Wp[idx] += h
+            Wm = W.copy(); Wm[idx] -= h
+            args_p = (Wp, W2) if W is W1 else (W1, Wp)
+            args_m = (Wm, W2) if W is W1 else (W1, Wm)
+            fd = (scf.mlp_loss_grad(*args_p, X, T)[0] - scf.mlp_loss_grad(*args_m, X, T)[0]) / (2 * h)
+            assert g[idx] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_mlp_is_positively_homogeneous():
+    rng = np.random.default_rng(1)
+    W1 = rng.standard_normal((6, 4))
+    W2 = rng.standard_normal((4, 6))
+    X = rng.standard_normal((3, 4))
+    assert np.allclose(scf.mlp_forward(W1, W2, 3.5 * X), 3.5 * scf.mlp_forward(W1, W2, X))
+
+
+def test_adam_matches_definition():
+    w, g = np.array([1.0, -2.0]), np.array([0.5, 0.25])
+    m, v = np.zeros(2), np.zeros(2)
+    w1, m1, v1 = scf.adam_step(w, g, m, v, 1, 0.1)
+    # first step: m_hat = g, v_hat = g^2 -> w - lr * g / (|g| + eps) = w - lr * sign(g)
+    assert np.allclose(w1, w - 0.1 * np.sign(g), atol=1e-7)

@@ -184,3 +184,26 @@ def metallic_spectrum(n: int = 8192, k: int = 256, seed: int = 0) -> RandomSpect
     a = sym_gaussian(rng, n, sig)
     h1 = np.stack([sym_gaussian(rng, n, sig) for _ in range(k)]) if k else np.zeros((0, n, n))
     return RandomSpectrumProblem(H=h, Q=q, e=e, A=a, H1=h1, nocc=n // 2)
+
+
+def site_kernel(tb: TightBinding, kind: str = "regularised") -> np.ndarray:
+    """Site-site interaction kernel K (n_sites x n_sites) of the
+    self-consistent response workload, from minimum-image distances r_ab:
+    'literal':     K_ab = 1 on the diagonal, 1 / r_ab off it;
+    'regularised': K_ab = 1 / sqrt(r_ab^2 + 1) (same diagonal, positive definite)."""
+    p = tb.pos
+    d = p[:, None, :] - p[None, :, :]
+    d -= tb.box * np.round(d / tb.box)
+    r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+    if kind == "literal":
+        with np.errstate(divide="ignore"):
+            K = np.where(np.eye(len(p), dtype=bool), 1.0, 1.0 / np.where(r > 0, r, 1.0))
+        return K
+    return 1.0 / np.sqrt(r * r + 1.0)
+
+
+def site_fields(tb: TightBinding, f: int, sigma: float = 0.1, seed: int = 2) -> np.ndarray:
+    """F external site potentials V_ext ~ N(0, sigma^2), shape (F, n_sites).
+    Draw order: F * n_sites normals, row-major."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((f, tb.n // tb.norb)) * sigma
