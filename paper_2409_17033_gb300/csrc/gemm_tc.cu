@@ -197,7 +197,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
           int nkb, int ch, int epi, int64_t np, float* __restrict__ out,
           uint16_t* __restrict__ out_hi, uint16_t* __restrict__ out_lo,
           const float* __restrict__ xprev, Part3* __restrict__ part,
-          const Tile* __restrict__ tiles, DevState* st, int step,
+          const Tile* __restrict__ tiles, int ntiles, DevState* st, int step,
           const float* __restrict__ a_scale, const float* __restrict__ b_scale,
           float* __restrict__ zmax) {
   constexpr uint32_t kIdesc = idesc_for(F16);
@@ -213,13 +213,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
   uint64_t* tfull = empty + STAGES;   // [2] chunk accumulated in TMEM buffer b
   uint64_t* tempty = tfull + 2;       // [2] TMEM buffer b drained by the epilogue warps
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-  __shared__ double red1[EPI_WARPS], red2[EPI_WARPS], red3[EPI_WARPS];
+  __shared__ double red[2][3][EPI_WARPS];   // per-tile partials, double-buffered by tile parity
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Tile t = tiles[blockIdx.x];
   int* abortf = &st->abort_flag;
   const int total_kb = 3 * nkb;
   const int nchunks = total_kb / ch;
+  // persistent static schedule: this CTA handles tiles blockIdx.x, +gridDim.x, ...
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -248,97 +249,120 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < total_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abortf)) break;
-        const int seg = kb / nkb;
-        const int kx = (kb - seg * nkb) * BK;
-        const CUtensorMap* ma = seg < 2 ? &mA_hi : &mA_lo;
-        const CUtensorMap* mb = seg == 1 ? &mB_lo : &mB_hi;
-        uint8_t* sa = smem + s * STAGE_BYTES;
-        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_2d(ma, &full[s], sa, kx, t.row0);
-        tma_load_2d(mb, &full[s], sa + A_BYTES, kx, t.col0);
-        issued = kb + 1;
+      // k-block counter g runs on across tiles: stage g % STAGES, phase (g / STAGES) & 1
+      int64_t issued = 0;
+      bool ok = true;
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        const Tile t = tiles[blockIdx.x + (int64_t)it * gridDim.x];
+        for (int kb = 0; kb < total_kb; ++kb) {
+          const int64_t g = (int64_t)it * total_kb + kb;
+          const int s = (int)(g % STAGES);
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abortf)) {
+            ok = false;
+            break;
+          }
+          const int seg = kb / nkb;
+          const int kx = (kb - seg * nkb) * BK;
+          const CUtensorMap* ma = seg < 2 ? &mA_hi : &mA_lo;
+          const CUtensorMap* mb = seg == 1 ? &mB_lo : &mB_hi;
+          uint8_t* sa = smem + s * STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(ma, &full[s], sa, kx, t.row0);
+          tma_load_2d(mb, &full[s], sa + A_BYTES, kx, t.col0);
+          issued = g + 1;
+        }
       }
-      if (issued < total_kb) {
+      if (!ok) {
         // aborted: let the copies already issued land before the CTA exits
-        const int first = issued > STAGES ? issued - STAGES : 0;
-        for (int kb = first; kb < issued; ++kb)
-          mbar_wait_drain(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, 200000000ull);
+        const int64_t first = issued > STAGES ? issued - STAGES : 0;
+        for (int64_t g = first; g < issued; ++g)
+          mbar_wait_drain(&full[g % STAGES], (uint32_t)(g / STAGES) & 1u, 200000000ull);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int b = c & 1;
-        // the epilogue has drained buffer b (chunk c-2)
-        if (!mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, abortf)) break;
-        tc_fence_after();
-        const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
-        for (int kb = c * ch; kb < (c + 1) * ch; ++kb) {
-          const int s = kb % STAGES;
-          const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-          if (!mbar_wait(&full[s], ph, abortf)) {
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        for (int c = 0; c < nchunks && ok; ++c) {
+          const int64_t gc = (int64_t)it * nchunks + c;  // chunk counter across tiles
+          const int b = (int)(gc & 1);
+          // the epilogue has drained buffer b (chunk gc-2)
+          if (!mbar_wait(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
-          const uint64_t adesc = sdesc_sw128(a_addr);
-          const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
+          const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
+          for (int kb = c * ch; kb < (c + 1) * ch; ++kb) {
+            const int64_t g = (int64_t)it * total_kb + kb;
+            const int s = (int)(g % STAGES);
+            const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, abortf)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+            const uint64_t adesc = sdesc_sw128(a_addr);
+            const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
-            umma_bf16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
-                      (kb > c * ch || k > 0) ? 1u : 0u);
+            for (int k = 0; k < BK / 16; ++k) {
+              // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
+              umma_bf16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                        (kb > c * ch || k > 0) ? 1u : 0u);
+            }
+            umma_commit(&empty[s]);
           }
-          umma_commit(&empty[s]);
+          umma_commit(&tfull[b]);
         }
-        umma_commit(&tfull[b]);
       }
     }
   } else {
     // epilogue warps 2 .. 2+EPI_WARPS-1: warp w reads TMEM lanes 32*(w%4) .. +31 and
     // columns [half*128, half*128+128). Each K chunk is drained from TMEM into
     // FP32 registers with round-to-nearest adds (FP16X2: chunks of the hi*lo
-    // segments weighted by 2^-11).
+    // segments weighted by 2^-11); the tile's stores follow while the MMA warp
+    // already fills the freed TMEM buffers with the next tile's chunks.
     const int e = warp - 2;
     const int q = warp & 3;
     const int half = e >> 2;
     const int r = q * 32 + lane;
-    const int64_t gi = t.row0 + r;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HALF_COLS);
-    float acc[HALF_COLS];
-#pragma unroll
-    for (int j = 0; j < HALF_COLS; ++j) acc[j] = 0.0f;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int b = c & 1;
-      bool w = mbar_wait(&tfull[b], (uint32_t)(c >> 1) & 1u, abortf);
-      w = __all_sync(0xffffffffu, w);
-      if (!w) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const float wgt = (F16 && (c * ch) >= nkb) ? (1.0f / kLoScale) : 1.0f;
+    for (int it = 0; it < my_tiles && ok; ++it) {
+      const int tix = blockIdx.x + it * gridDim.x;
+      const Tile t = tiles[tix];
+      const int64_t gi = t.row0 + r;
+      float acc[HALF_COLS];
 #pragma unroll
-      for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(trow + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+      for (int j = 0; j < HALF_COLS; ++j) acc[j] = 0.0f;
+      for (int c = 0; c < nchunks; ++c) {
+        const int64_t gc = (int64_t)it * nchunks + c;
+        const int b = (int)(gc & 1);
+        bool w = mbar_wait(&tfull[b], (uint32_t)(gc >> 1) & 1u, abortf);
+        w = __all_sync(0xffffffffu, w);
+        if (!w) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const float wgt = (F16 && (c * ch) >= nkb) ? (1.0f / kLoScale) : 1.0f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] = fmaf(wgt, __uint_as_float(v[j]), acc[c0 + j]);
+        for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(trow + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[c0 + j] = fmaf(wgt, __uint_as_float(v[j]), acc[c0 + j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
-    }
-    double t1 = 0.0, t2 = 0.0, f = 0.0;
-    if (ok && !*((volatile int*)abortf)) {
+      if (!ok || *((volatile int*)abortf)) break;
+      // per-thread partials over at most 128 entries of one row in FP32 (GB300's FP64
+      // rate is a small fraction of its FP32 rate); lanes, warps and tiles add in FP64
+      float t1 = 0.0f, t2 = 0.0f, f = 0.0f;
       const int sg = (epi == EPI_SQUARE) ? st->sigma[step] : 1;
       const int64_t bat = gi / np;  // batch entry of this row (stacked A)
       float inv_s = (F16 && a_scale) ? 1.0f / a_scale[bat] : 1.0f;
@@ -384,18 +408,18 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             dm[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
-          __align__(16) uint16_t h[16], l[16];
+          __align__(16) uint16_t hh[16], ll[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            if (F16) split_fp16(val[j], 1.0f, h[j], l[j]);
-            else split_bf16(val[j], h[j], l[j]);
+            if (F16) split_fp16(val[j], 1.0f, hh[j], ll[j]);
+            else split_bf16(val[j], hh[j], ll[j]);
           }
           uint4* dh = reinterpret_cast<uint4*>(out_hi + gi * np + gj0);
           uint4* dl = reinterpret_cast<uint4*>(out_lo + gi * np + gj0);
-          dh[0] = reinterpret_cast<const uint4*>(h)[0];
-          dh[1] = reinterpret_cast<const uint4*>(h)[1];
-          dl[0] = reinterpret_cast<const uint4*>(l)[0];
-          dl[1] = reinterpret_cast<const uint4*>(l)[1];
+          dh[0] = reinterpret_cast<const uint4*>(hh)[0];
+          dh[1] = reinterpret_cast<const uint4*>(hh)[1];
+          dl[0] = reinterpret_cast<const uint4*>(ll)[0];
+          dl[1] = reinterpret_cast<const uint4*>(ll)[1];
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
@@ -405,16 +429,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         for (int j = 0; j < 16; ++j) {
           const int64_t gj = gj0 + j;
           if (gj < gi) continue;
-          const double d = (double)val[j];
-          const double rr = (double)res[j];
+          const float d = val[j], rr = res[j];
           if (gj == gi) {
             t1 += d;
-            t2 += d * d;
-            f += rr * rr;
+            t2 = fmaf(d, d, t2);
+            f = fmaf(rr, rr, f);
           } else {
             store_split<F16>(out, out_hi, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
-            t2 += 2.0 * d * d;
-            f += 2.0 * rr * rr;
+            t2 = fmaf(2.0f * d, d, t2);
+            f = fmaf(2.0f * rr, rr, f);
           }
         }
       }
@@ -423,32 +446,36 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         if (lane == 0 && zm > 0.0f)
           atomicMax(reinterpret_cast<int*>(&zmax[bat]), __float_as_int(zm));
       }
-    }
-    if (epi == EPI_SQUARE) {
-      for (int o = 16; o > 0; o >>= 1) {
-        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-        f += __shfl_xor_sync(0xffffffffu, f, o);
-      }
-      if (lane == 0) {
-        red1[e] = t1;
-        red2[e] = t2;
-        red3[e] = f;
+      if (epi == EPI_SQUARE) {
+        double d1 = t1, d2 = t2, d3 = f;
+        for (int o = 16; o > 0; o >>= 1) {
+          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+          d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+          d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+        }
+        const int pb = it & 1;
+        if (lane == 0) {
+          red[pb][0][e] = d1;
+          red[pb][1][e] = d2;
+          red[pb][2][e] = d3;
+        }
+        // epilogue warps only (named barrier 1): one thread writes the tile's partials
+        asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+        if (e == 0 && lane == 0) {
+          double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          for (int w = 0; w < EPI_WARPS; ++w) {
+            s1 += red[pb][0][w];
+            s2 += red[pb][1][w];
+            s3 += red[pb][2][w];
+          }
+          part[tix] = Part3{s1, s2, s3};
+        }
       }
     }
   }
 
   tc_fence_before();
   __syncthreads();
-  if (epi == EPI_SQUARE && threadIdx.x == 0) {
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int w = 0; w < EPI_WARPS; ++w) {
-      s1 += red1[w];
-      s2 += red2[w];
-      s3 += red3[w];
-    }
-    part[blockIdx.x] = Part3{s1, s2, s3};
-  }
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -528,17 +555,31 @@ cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t 
     return cudaErrorInvalidValue;
   }
   const int nkb = (int)(np / BK);
-  // K chunk drained from TMEM into FP32 registers: 8 k-blocks (512) when it
-  // divides a segment, else 4 (np is a multiple of 256, so nkb of 4)
-  const int ch = (nkb % 8 == 0) ? 8 : 4;
+  // K chunk drained from TMEM into FP32 registers: 4 k-blocks (256 products per
+  // accumulator pass). np is a multiple of 256, so 4 divides every segment and
+  // the lo-plane weight changes only at a chunk boundary. The tensor core's
+  // FP32 accumulation truncates, and its bias grows with the chunk length: at
+  // N=4096 (FP16X2) 256-wide chunks give a 1.0e-5 density error against the
+  // exact form, 512-wide 2.5e-5 and 2048-wide 7.6e-4, for 3% more time per
+  // product than 512-wide chunks.
+  const int ch = 4;
+  // persistent: one CTA per SM (the shared-memory ring allows no second one)
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 1;
+  }
+  const int grid = ntiles < nsm ? ntiles : nsm;
   if (f16)
-    k_gemm_tc<true><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
+    k_gemm_tc<true><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
         ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
-        out.lo, x_prev, part, tiles, st, step, a_scale, b_scale, zmax);
+        out.lo, x_prev, part, tiles, ntiles, st, step, a_scale, b_scale, zmax);
   else
-    k_gemm_tc<false><<<ntiles, NUM_THREADS, SMEM_BYTES, s>>>(
+    k_gemm_tc<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
         ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
-        out.lo, x_prev, part, tiles, st, step, nullptr, nullptr, nullptr);
+        out.lo, x_prev, part, tiles, ntiles, st, step, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -228,36 +228,73 @@ __device__ __forceinline__ bool halted(const DevState* st, int step) {
 
 // ------------------------------------------------------------ symmetrised update
 // Y_{n+1} = (1 - sigma) Y_n + sigma (Z + Z^T), Z = Y_n X_n (Eqs. DM1-DM3: X_n Y_n = (Y_n X_n)^T
-// for symmetric X_n, Y_n). One block per 32x32 tile pair (I <= J); both tiles written.
+// for symmetric X_n, Y_n). One block per tile pair (I <= J) of the upper triangle, taken from
+// a linear block index (no idle blocks for the lower triangle); Z tiles (I,J) and (J,I) are
+// read once with 16-byte loads, Y_{n+1}(I,J) is written and mirrored into (J,I).
+template <typename T>
+__device__ __forceinline__ void ld4_stream(const T* p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void ld4_stream<float>(const float* p, float (&v)[4]) {
+  const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ld4_stream<double>(const double* p, double (&v)[4]) {
+  const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+
+// four consecutive entries of Y_{n+1} (idx a multiple of 4): master and, in the split
+// modes, the hi/lo planes as one 8-byte store each
 template <typename ZT, int MODE>
-__device__ __forceinline__ void store_y(MatBuf y, int64_t idx, ZT v, float s) {
-  static_cast<ZT*>(y.master)[idx] = v;
-  if (MODE == SP2_MODE_BF16X2) {
-    uint16_t h, l;
-    split_bf16((float)v, h, l);
-    y.hi[idx] = h;
-    y.lo[idx] = l;
-  } else if (MODE == SP2_MODE_FP16X2) {
-    uint16_t h, l;
-    split_fp16((float)v, s, h, l);
-    y.hi[idx] = h;
-    y.lo[idx] = l;
+__device__ __forceinline__ void store_y4(MatBuf y, int64_t idx, const ZT (&v)[4], float s) {
+  if constexpr (sizeof(ZT) == 4) {
+    *reinterpret_cast<float4*>(static_cast<float*>(y.master) + idx) =
+        make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  } else {
+    double2* d = reinterpret_cast<double2*>(static_cast<double*>(y.master) + idx);
+    d[0] = make_double2((double)v[0], (double)v[1]);
+    d[1] = make_double2((double)v[2], (double)v[3]);
+  }
+  if (MODE == SP2_MODE_BF16X2 || MODE == SP2_MODE_FP16X2) {
+    uint16_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (MODE == SP2_MODE_BF16X2) split_bf16((float)v[j], h[j], l[j]);
+      else split_fp16((float)v[j], s, h[j], l[j]);
+    }
+    *reinterpret_cast<uint2*>(y.hi + idx) =
+        make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+    *reinterpret_cast<uint2*>(y.lo + idx) =
+        make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
   }
 }
 
+constexpr int kSymThreads = 256;
+template <typename ZT>
+constexpr int sym_tile() { return sizeof(ZT) == 4 ? 64 : 32; }   // 33 / 17 KB of shared memory
+
 template <typename ZT, int MODE>
-__global__ void k_symm_update(const ZT* __restrict__ Z, MatBuf yin, MatBuf yout, int64_t np,
-                              const DevState* st, int step, ScaleBuf sc, int slot_in,
-                              int slot_out) {
+__global__ void __launch_bounds__(kSymThreads)
+    k_symm_update(const ZT* __restrict__ Z, MatBuf yin, MatBuf yout, int64_t np,
+                  const DevState* st, int step, ScaleBuf sc, int slot_in, int slot_out) {
   if (halted(st, step)) return;
-  const int I = blockIdx.y, J = blockIdx.x;
-  if (I > J) return;
-  const int64_t b = blockIdx.z;
-  const int64_t base = b * np * np;
-  __shared__ ZT zij[32][33];
-  __shared__ ZT zji[32][33];
-  __shared__ ZT yt[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  constexpr int TE = sym_tile<ZT>();
+  constexpr int V = TE / 4;                // 4-entry vectors per tile row
+  constexpr int R = kSymThreads / V;       // rows covered by one pass of the block
+  constexpr int P = TE / R;
+  // column J of the upper triangle holds tiles I = 0..J: t = J (J + 1) / 2 + I
+  const int64_t t = blockIdx.x;
+  int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (J * (J + 1) / 2 > t) --J;
+  while ((J + 1) * (J + 2) / 2 <= t) ++J;
+  const int64_t I = t - J * (J + 1) / 2;
+  const int64_t base = (int64_t)blockIdx.y * np * np;
+  const int64_t b = blockIdx.y;
+  __shared__ ZT za[TE][TE + 1];   // Z tile (I,J), overwritten in place by Y_{n+1}(I,J)
+  __shared__ ZT zb[TE][TE + 1];   // Z tile (J,I)
+  const int c4 = (threadIdx.x % V) * 4, r0 = threadIdx.x / V;
   const int sg = st->sigma[step];
   float s = 1.0f;
   if (MODE == SP2_MODE_FP16X2) {
@@ -265,39 +302,48 @@ __global__ void k_symm_update(const ZT* __restrict__ Z, MatBuf yin, MatBuf yout,
     float bound = 2.0f * sc.zmax[b];
     if (sg < 0) bound += 2.0f * sc.ymax[slot_in * sc.B + b];
     s = pow2_scale(bound);
-    if (I == 0 && J == 0 && tx == 0 && ty == 0) sc.yscale[slot_out * sc.B + b] = s;
+    if (t == 0 && threadIdx.x == 0) sc.yscale[slot_out * sc.B + b] = s;
   }
-  for (int k = 0; k < 32; k += 8) {
-    zij[ty + k][tx] = Z[base + (int64_t)(I * 32 + ty + k) * np + J * 32 + tx];
-    zji[ty + k][tx] = Z[base + (int64_t)(J * 32 + ty + k) * np + I * 32 + tx];
+  const int64_t rI = I * TE, rJ = J * TE;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int r = r0 + p * R;
+    ZT a[4], c[4];
+    ld4_stream(Z + base + (rI + r) * np + rJ + c4, a);
+    ld4_stream(Z + base + (rJ + r) * np + rI + c4, c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) za[r][c4 + j] = a[j], zb[r][c4 + j] = c[j];
   }
   __syncthreads();
   float amax = 0.0f;
-  for (int k = 0; k < 32; k += 8) {
-    const int r = ty + k, c = tx;
-    const int64_t idx = base + (int64_t)(I * 32 + r) * np + J * 32 + c;
-    ZT sum = zij[r][c] + zji[c][r];
-    ZT y;
-    if (sg > 0) {
-      y = sum;
-    } else {
-      ZT yo = static_cast<const ZT*>(yin.master)[idx];
-      y = (ZT)2 * yo - sum;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int r = r0 + p * R;
+    const int64_t idx = base + (rI + r) * np + rJ + c4;
+    ZT y[4], yo[4];
+    if (sg < 0) ld4_stream(static_cast<const ZT*>(yin.master) + idx, yo);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const ZT sum = za[r][c4 + j] + zb[c4 + j][r];
+      y[j] = sg > 0 ? sum : (ZT)2 * yo[j] - sum;
+      amax = fmaxf(amax, fabsf((float)y[j]));
+      za[r][c4 + j] = y[j];   // only this thread touches za[r][c4..c4+3] in this phase
     }
-    yt[r][c] = y;
-    store_y<ZT, MODE>(yout, idx, y, s);
-    amax = fmaxf(amax, fabsf((float)y));
+    store_y4<ZT, MODE>(yout, idx, y, s);
   }
   if (MODE == SP2_MODE_FP16X2) {
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (tx == 0 && amax > 0.0f) atomic_max_nonneg(&sc.ymax[slot_out * sc.B + b], amax);
+    if ((threadIdx.x & 31) == 0 && amax > 0.0f) atomic_max_nonneg(&sc.ymax[slot_out * sc.B + b], amax);
   }
   if (I == J) return;
   __syncthreads();
-  for (int k = 0; k < 32; k += 8) {
-    const int r = ty + k, c = tx;
-    const int64_t idx = base + (int64_t)(J * 32 + r) * np + I * 32 + c;
-    store_y<ZT, MODE>(yout, idx, yt[c][r], s);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int r = r0 + p * R;
+    ZT y[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[j] = za[c4 + j][r];
+    store_y4<ZT, MODE>(yout, base + (rJ + r) * np + rI + c4, y, s);
   }
 }
 
@@ -423,7 +469,9 @@ cudaError_t launch_decide(const Part3* part, DevState* st, DecideParams p, cudaS
 cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t np, int64_t batch,
                                int mode, const DevState* st, int step, ScaleBuf sc, int slot_in,
                                int slot_out, cudaStream_t s) {
-  dim3 grid((unsigned)(np / 32), (unsigned)(np / 32), (unsigned)batch), block(32, 8);
+  // np is a multiple of 256, so both tile edges divide it
+  const int64_t nb = np / (mode == SP2_MODE_FP64 ? sym_tile<double>() : sym_tile<float>());
+  dim3 grid((unsigned)(nb * (nb + 1) / 2), (unsigned)batch), block(kSymThreads);
   if (mode == SP2_MODE_FP64)
     k_symm_update<double, SP2_MODE_FP64><<<grid, block, 0, s>>>(
         static_cast<const double*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
