@@ -59,6 +59,7 @@ extern "C" {
 #endif
 
 #define SP2_MAX_ITER 256
+#define SP2_CKPT_AUTO (-1)  /* sp2_opts.ckpt_k: choose k from free device memory */
 
 typedef enum {
   SP2_OK = 0,
@@ -110,7 +111,11 @@ typedef struct {
   double eps_min;      /* if eps_min < eps_max: spectral bounds to use instead of the */
   double eps_max;      /* Gershgorin estimate (Sec. II: alpha, beta from eps_min/eps_max) */
   int ckpt_k;          /* sp2_density keep_history / backward chi: keep X_n every ckpt_k
-                          steps (1 = all), recompute the rest per segment (0 = default 4) */
+                          steps and recompute the rest per segment (0 = default 4). 1 keeps
+                          every X_n (split modes: its hi/lo planes) and recomputes nothing.
+                          SP2_CKPT_AUTO: the smallest k whose history of max_iter steps fits
+                          in free device memory (and the workspace limit) beside the working
+                          set, so X_n is recomputed only when the history outgrows HBM. */
   int keep_history;    /* sp2_density: keep the X_n checkpoints for a later sp2_adjoint */
   int time_kernels;    /* 1: bracket every product-kernel launch with CUDA events on the
                           handle's stream and report their summed duration in sp2_info */
@@ -135,6 +140,8 @@ typedef struct {
   double product_ms;                  /* time_kernels: summed event time of the product launches
                                          that did work, else 0 */
   int64_t product_launches_timed;
+  int ckpt_k;                         /* checkpoint interval the call used (backward chi and
+                                         keep_history; SP2_CKPT_AUTO resolved), else 0 */
 } sp2_info;
 
 typedef struct sp2_handle_s* sp2_handle_t;

@@ -25,6 +25,7 @@ F64, F32 = 0, 1
 # sp2_mode
 MODE_FP64, MODE_FP32, MODE_BF16X2, MODE_FP16X2 = 0, 1, 2, 3
 MODES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16x2": MODE_BF16X2, "fp16x2": MODE_FP16X2}
+CKPT_AUTO = -1   # SP2_CKPT_AUTO
 
 
 class Opts(C.Structure):
@@ -63,6 +64,7 @@ class Info(C.Structure):
         ("kernel_launches", C.c_int64),
         ("product_ms", C.c_double),
         ("product_launches_timed", C.c_int64),
+        ("ckpt_k", C.c_int),
     ]
 
     def to_dict(self) -> dict:
@@ -85,6 +87,7 @@ class Info(C.Structure):
             "kernel_launches": int(self.kernel_launches),
             "product_ms": float(self.product_ms),
             "product_launches_timed": int(self.product_launches_timed),
+            "ckpt_k": int(self.ckpt_k),
         }
 
 

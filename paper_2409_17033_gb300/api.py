@@ -33,11 +33,12 @@ SP2Error = L.SP2Error
 
 
 def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: float = -1.0,
-              max_iter: int = 0, min_iter: int = -1, sigma=None, bounds=None, ckpt_k: int = 0,
-              keep_history: bool = False, time_kernels: bool = False):
+              max_iter: int = 0, min_iter: int = -1, sigma=None, bounds=None,
+              ckpt_k: int | str = 0, keep_history: bool = False, time_kernels: bool = False):
     """sp2_opts with the library defaults for everything not given. Returns
     (opts, keepalive) where keepalive holds the branch array referenced by
-    opts.sigma_in."""
+    opts.sigma_in. ckpt_k="auto" selects SP2_CKPT_AUTO (keep as much of the
+    X_n history as device memory holds)."""
     lib = L.load()
     o = L.Opts()
     lib.sp2_default_opts(C.byref(o))
@@ -46,7 +47,7 @@ def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: flo
     o.floor_gate = float(floor_gate)
     o.max_iter = int(max_iter)
     o.min_iter = int(min_iter)
-    o.ckpt_k = int(ckpt_k)
+    o.ckpt_k = L.CKPT_AUTO if ckpt_k == "auto" else int(ckpt_k)
     o.keep_history = 1 if keep_history else 0
     o.time_kernels = 1 if time_kernels else 0
     keep = None

@@ -347,6 +347,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
           break;
         }
         tc_fence_after();
+        if (epi == EPI_SQUARE && c == nchunks - 2) {
+          // the X_n entries the tile-end epilogue reads (512 B of this thread's row):
+          // pulled into L2 two chunks ahead, while the MMA warp can run only one
+          // chunk ahead of the epilogue
+          const float* xr = xprev + gi * np + t.col0 + half * HALF_COLS;
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xr),
+                       "r"((uint32_t)(HALF_COLS * sizeof(float)))
+                       : "memory");
+        }
         const float wgt = (F16 && (c * ch) >= nkb) ? (1.0f / kLoScale) : 1.0f;
 #pragma unroll
         for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {

@@ -3,6 +3,7 @@
 // every arithmetic step (bounds, scaling, products, branch choice, stopping
 // test, response updates, contractions) runs on the device.
 #include <stdarg.h>
+#include <algorithm>
 #include <cmath>
 #include <stdio.h>
 #include <string.h>
@@ -364,6 +365,37 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
   return SP2_OK;
 }
 
+// With every X_n kept (k = 1) in a split mode, the checkpoint holds the hi/lo planes
+// (np^2 x 4 bytes, the size of the FP32 master) instead of the master.
+bool ckpt_planes(int mode, int k) { return k == 1 && split_mode(mode); }
+
+// SP2_CKPT_AUTO: the smallest checkpoint interval k whose kept history fits in device
+// memory next to the working set, so X_n is recomputed only when the history of
+// max_iter steps would outgrow it. Working set reserved: X ping-pong, the adjoint's G
+// ping-pong and product output for `batch` matrices, the k-step segment and 1 GiB.
+int resolve_ckpt(sp2_handle_t h, sp2_opts* o, int64_t np, int64_t batch) {
+  if (o->ckpt_k != SP2_CKPT_AUTO) return SP2_OK;
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  double avail = (double)fr;
+  if (h->limit) avail = std::min(avail, (double)h->limit - (double)h->held);
+  const double el = (double)np * (double)np;
+  const double ms = (double)master_size(o->mode), mat_b = el * (ms + (split_mode(o->mode) ? 4 : 0));
+  const double b = (double)(batch > 0 ? batch : 1);
+  avail -= 2.0 * mat_b + 2.0 * b * mat_b + b * el * ms + (double)(1ull << 30);
+  const int cap = o->fixed_m > 0 ? o->fixed_m : o->max_iter;
+  int k = cap;
+  for (int kk = 1; kk <= cap; ++kk) {
+    const double need = (double)((cap + kk - 1) / kk) * el * ms + (double)(kk - 1) * mat_b;
+    if (need <= avail) {
+      k = kk;
+      break;
+    }
+  }
+  o->ckpt_k = k;
+  return SP2_OK;
+}
+
 int validate_opts(sp2_handle_t h, const sp2_opts* o) {
   if (o->mode != SP2_MODE_FP64 && o->mode != SP2_MODE_FP32 && o->mode != SP2_MODE_BF16X2 &&
       o->mode != SP2_MODE_FP16X2)
@@ -376,7 +408,8 @@ int validate_opts(sp2_handle_t h, const sp2_opts* o) {
     for (int i = 0; i < o->fixed_m; ++i)
       if (o->sigma_in[i] != 1 && o->sigma_in[i] != -1)
         return fail(h, SP2_EINVAL, "sigma_in[%d] = %d is not +-1", i, (int)o->sigma_in[i]);
-  if (o->ckpt_k < 1) return fail(h, SP2_EINVAL, "ckpt_k must be >= 1");
+  if (o->ckpt_k < 1 && o->ckpt_k != SP2_CKPT_AUTO)
+    return fail(h, SP2_EINVAL, "ckpt_k must be >= 1 or SP2_CKPT_AUTO");
   return SP2_OK;
 }
 
@@ -510,7 +543,15 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
     if (keep && (step - 1) % o.ckpt_k == 0) {
       void* ck;
       TRY(ws(h, "ckpt." + std::to_string((step - 1) / o.ckpt_k), xbytes, &ck));
-      CK(cudaMemcpyAsync(ck, xin.master, xbytes, cudaMemcpyDeviceToDevice, h->stream));
+      if (ckpt_planes(mode, o.ckpt_k)) {
+        // every X_n kept: its 16-bit planes are all the adjoint products read
+        const size_t pb = (size_t)np * np * 2;
+        CK(cudaMemcpyAsync(ck, xin.hi, pb, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(static_cast<char*>(ck) + pb, xin.lo, pb, cudaMemcpyDeviceToDevice,
+                           h->stream));
+      } else {
+        CK(cudaMemcpyAsync(ck, xin.master, xbytes, cudaMemcpyDeviceToDevice, h->stream));
+      }
     }
     if (ybatch > 0)
       TRY(response_step(c, xin, Y[step % 2], Y[(step + 1) % 2], ybatch, step, sc, step % 2,
@@ -634,8 +675,18 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
     CK(launch_split_scaled(G[gs], np, sc, gs, h->stream));
     c.kernels += 2;
   }
+  // segment buffers X_{s0+1} .. X_{s0+k-1}; X_{s0} is read from its checkpoint in place
+  // (the master) with its planes split into seg[0], or taken as the kept planes
+  const bool planes = ckpt_planes(mode, k);
   std::vector<MatBuf> seg(k);
-  for (int i = 0; i < k; ++i) TRY(mat(h, "seg." + std::to_string(i), np, np, mode, &seg[i]));
+  for (int i = 1; i < k; ++i) TRY(mat(h, "seg." + std::to_string(i), np, np, mode, &seg[i]));
+  if (!planes && split_mode(mode)) {
+    void* p;
+    TRY(ws(h, "seg.0.h", (size_t)np * np * 2, &p));
+    seg[0].hi = static_cast<uint16_t*>(p);
+    TRY(ws(h, "seg.0.l", (size_t)np * np * 2, &p));
+    seg[0].lo = static_cast<uint16_t*>(p);
+  }
   const size_t xbytes = (size_t)np * np * master_size(mode);
   const int nseg = (M + k - 1) / k;
   for (int j = nseg - 1; j >= 0; --j) {
@@ -643,10 +694,16 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
     const int s1 = (j * k + k) < M ? (j * k + k) : M;
     void* ck;
     TRY(ws(h, "ckpt." + std::to_string(j), xbytes, &ck));
-    CK(cudaMemcpyAsync(seg[0].master, ck, xbytes, cudaMemcpyDeviceToDevice, h->stream));
-    if (split_mode(mode)) {
-      CK(launch_split(seg[0], np, np, mode, h->stream));
-      c.kernels++;
+    if (planes) {
+      seg[0].master = nullptr;
+      seg[0].hi = static_cast<uint16_t*>(ck);
+      seg[0].lo = seg[0].hi + (size_t)np * np;
+    } else {
+      seg[0].master = ck;
+      if (split_mode(mode)) {
+        CK(launch_split(seg[0], np, np, mode, h->stream));
+        c.kernels++;
+      }
     }
     for (int s = s0; s < s1; ++s) {
       int nparts;
@@ -855,7 +912,10 @@ int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc
   MatBuf X[2], Y[2];
   Sp2Out r;
   const bool keep = o.keep_history != 0;
-  if (keep) h->hist.valid = false;
+  if (keep) {
+    h->hist.valid = false;
+    TRY(resolve_ckpt(h, &o, np, 1));
+  }
   TRY(run_sp2(h, Hd, N, dtype, nocc, o, nullptr, 0, 0, keep, X, Y, c, &r));
   CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
   c.kernels++;
@@ -874,6 +934,7 @@ int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc
     hs.beta = r.beta;
     hs.sigma.assign(r.M + 1, 0);
     for (int i = 1; i <= r.M; ++i) hs.sigma[i] = h->h_state->sigma[i];
+    if (info) info->ckpt_k = o.ckpt_k;
   }
   if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
   return SP2_OK;
@@ -956,6 +1017,7 @@ int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, doub
   MatBuf X[2], Y[2];
   Sp2Out r;
   h->hist.valid = false;
+  TRY(resolve_ckpt(h, &o, np, L));
   TRY(run_sp2(h, Hd, N, dtype, nocc, o, nullptr, 0, 0, true, X, Y, c, &r));
   if (D) {
     CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
@@ -980,6 +1042,7 @@ int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, doub
   }
   CK(cudaStreamSynchronize(h->stream));
   fill_timing(c, r.M, info);
+  if (info) info->ckpt_k = o.ckpt_k;
   if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
   return SP2_OK;
 }

@@ -95,6 +95,24 @@ def test_fp64_backward_checkpoint_segments(sp2, c1, k):
     assert rel(host(chi_b[0]), ref) < 1e-10
 
 
+@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2", "fp32"])
+def test_checkpoint_policies_agree_bitwise(sp2, c1, mode):
+    """Keeping every X_n (split modes: its hi/lo planes), every 3rd with segment
+    recompute, and the memory-sized automatic choice run the same products on
+    the same operands, so chi is bit-identical; at N=128 the automatic choice
+    keeps every step."""
+    p, _ = c1
+    H = cuda(p.H, torch.float32)
+    A = cuda(p.A[None], torch.float32)
+    out = {}
+    for k in (1, 3, "auto"):
+        chi, _, info = sp2.sp2_susceptibility(H, p.nocc, A, "backward", mode=mode, ckpt_k=k)
+        out[k] = (chi, info)
+    assert out["auto"][1]["ckpt_k"] == 1 and out[3][1]["ckpt_k"] == 3
+    assert torch.equal(out[1][0], out[3][0])
+    assert torch.equal(out[1][0], out["auto"][0])
+
+
 def test_fp64_response_batch_and_duality(sp2, c1):
     p, o = c1
     D1, _, info = sp2.sp2_response(cuda(p.H), p.nocc, cuda(p.H1), mode="fp64", idem_tol=1e-10)
