@@ -142,6 +142,8 @@ typedef struct {
   int64_t product_launches_timed;
   int ckpt_k;                         /* checkpoint interval the call used (backward chi and
                                          keep_history; SP2_CKPT_AUTO resolved), else 0 */
+  int refine_iter;                    /* sp2_scf_response: first iteration (0-based) computed
+                                         in refine_mode, -1 if none */
 } sp2_info;
 
 typedef struct sp2_handle_s* sp2_handle_t;
@@ -247,6 +249,13 @@ typedef struct {
   const float* W2;
   int hidden;           /* MLP width */
   int bf16_infer;       /* 1: bfloat16 operands in inference */
+  int refine_mode;      /* sp2_mode of the responses after the switch below */
+  double refine_below;  /* > 0: once the residual is <= refine_below, or has not reached a
+                           new minimum for 3 iterations, the remaining iterations compute
+                           the responses in refine_mode: its own SP2 run fixes the branches
+                           and M again, and Anderson restarts its history. 0 = never
+                           switch. Lets split-precision responses do the bulk of the
+                           iterations and FP32 / FP64 ones go below their rounding floor. */
 } sp2_scf_opts;
 
 int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc, int norb,

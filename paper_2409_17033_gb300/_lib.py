@@ -65,6 +65,7 @@ class Info(C.Structure):
         ("product_ms", C.c_double),
         ("product_launches_timed", C.c_int64),
         ("ckpt_k", C.c_int),
+        ("refine_iter", C.c_int),
     ]
 
     def to_dict(self) -> dict:
@@ -88,6 +89,7 @@ class Info(C.Structure):
             "product_ms": float(self.product_ms),
             "product_launches_timed": int(self.product_launches_timed),
             "ckpt_k": int(self.ckpt_k),
+            "refine_iter": int(self.refine_iter),
         }
 
 
@@ -102,6 +104,8 @@ class ScfOpts(C.Structure):
         ("W2", C.c_void_p),
         ("hidden", C.c_int),
         ("bf16_infer", C.c_int),
+        ("refine_mode", C.c_int),
+        ("refine_below", C.c_double),
     ]
 
 

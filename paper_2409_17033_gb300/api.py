@@ -235,10 +235,15 @@ def sp2_fermi(H, mu: float, kT: float, B=None, diag_only: bool = False, canonica
 def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
                      alpha: float = 0.3, history: int = 8, tol: float = 1e-6, max_iter: int = 100,
                      W1=None, W2=None, bf16_infer: bool = True, record: bool = False,
-                     mode="fp64", handle: Handle | None = None, allow_noconv: bool = False, **kw):
+                     mode="fp64", refine_mode=None, refine_below: float = 0.0,
+                     handle: Handle | None = None, allow_noconv: bool = False,
+                     return_info: bool = False, **kw):
     """Self-consistent site-charge response for F fields (rows of Vext, float64).
     K: (n_sites, n_sites) float64. Returns (q, residuals, iterations, (traj_r,
-    traj_q) or None); q and the trajectories live where Vext lives."""
+    traj_q) or None), plus the info dict when return_info; q and the
+    trajectories live where Vext lives. refine_mode / refine_below: compute the
+    responses in another arithmetic mode once the residual is below
+    refine_below or stalls (info["refine_iter"] = first such iteration)."""
     h = handle or default_handle()
     h.bind_stream()
     n = H.shape[0]
@@ -253,6 +258,9 @@ def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
     so.W2 = _ptr(W2) if W2 is not None else None
     so.hidden = int(W1.shape[0]) if W1 is not None else 0
     so.bf16_infer = 1 if bf16_infer else 0
+    if refine_mode is not None:
+        so.refine_mode = L.MODES[refine_mode] if isinstance(refine_mode, str) else int(refine_mode)
+        so.refine_below = float(refine_below)
     q = _empty_like(Vext, (F, ns))
     res = np.zeros(max_iter, dtype=np.float64)
     its = C.c_int(0)
@@ -269,7 +277,8 @@ def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
                                 _ptr(tq) if record else None, C.byref(info))
     h.check(rc, allow_noconv)
     k = its.value
-    return q, res[:k], k, ((tr[:k], tq[:k]) if record else None)
+    out = (q, res[:k], k, ((tr[:k], tq[:k]) if record else None))
+    return out + (info.to_dict(),) if return_info else out
 
 
 def mlp_forward(W1, W2, X, bf16: bool = False, handle: Handle | None = None):

@@ -1478,6 +1478,10 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   if (so->mixer < 0 || so->mixer > 2) return fail(h, SP2_EINVAL, "unknown mixer");
   sp2_opts o = resolve(opts_in);
   TRY(validate_opts(h, &o));
+  const bool refine = so->refine_below > 0.0 && so->refine_mode != o.mode;
+  if (refine && so->refine_mode != SP2_MODE_FP64 && so->refine_mode != SP2_MODE_FP32 &&
+      so->refine_mode != SP2_MODE_BF16X2 && so->refine_mode != SP2_MODE_FP16X2)
+    return fail(h, SP2_EINVAL, "unknown refine_mode %d", so->refine_mode);
   if (info) memset(info, 0, sizeof *info);
   const int64_t ns = N / norb, np = pad_n(N), tot = F * ns;
   const size_t mb = (size_t)N * N * dsize(dtype);
@@ -1531,6 +1535,12 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   int it = 0;
   bool done = false;
   std::vector<double> Gh, ch;
+  std::vector<int8_t> frozen;  // branch signs of the SP2 run that fixed the polynomial
+  bool frozen_here = false;    // the fixed polynomial is this loop's (not the caller's)
+  int a0 = 0;                  // first iteration of the current Anderson history
+  int refine_iter = -1;        // first iteration computed in refine_mode
+  double best = 0.0;           // smallest residual so far and iterations since it
+  int since_best = 0;
   for (; it < so->max_iter && !done; ++it) {
     // u = V + K q, perturbation diag(u (x) 1_norb), response, site charges
     CK(launch_site_potential(static_cast<const double*>(Vd), static_cast<const double*>(Kd), q, F,
@@ -1540,6 +1550,18 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
     Sp2Out rr;
     TRY(run_sp2(h, Hd, N, dtype, nocc, o, pub, F, 1, false, X, Y, c, &rr));
     if (!rr.converged) return fail(h, SP2_ENOCONV, "SP2 did not converge inside the SCF loop");
+    if (o.fixed_m == 0) {
+      // H is the same in every iteration: later iterations apply this run's polynomial
+      // -- its branches, M and spectral bounds -- so the response map changes only by
+      // rounding from one iteration to the next
+      frozen_here = true;
+      frozen.resize(rr.M);
+      for (int i = 1; i <= rr.M; ++i) frozen[i - 1] = (int8_t)h->h_state->sigma[i];
+      o.fixed_m = rr.M;
+      o.sigma_in = frozen.data();
+      o.eps_min = rr.emin;
+      o.eps_max = rr.emax;
+    }
     CK(launch_site_charges(Y[rr.yslot].master, o.mode, F, ns, norb, np, qo, h->stream));
     CK(cudaMemsetAsync(norms, 0, 2 * sizeof(double), h->stream));
     CK(launch_residual(qo, q, tot, r, norms, h->stream));
@@ -1560,11 +1582,33 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       done = true;
       break;
     }
-    if (so->mixer == SP2_MIX_LINEAR) {
+    if (it == 0 || res < best) {
+      best = res;
+      since_best = 0;
+    } else {
+      ++since_best;
+    }
+    if (refine && refine_iter < 0 && (res <= so->refine_below || since_best >= 3)) {
+      // the following iterations compute the responses in refine_mode
+      o.mode = so->refine_mode;
+      TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
+      if (frozen_here) {
+        // the refined arithmetic converges its own SP2 polynomial once (stop rule),
+        // which is then fixed again
+        o.fixed_m = 0;
+        o.sigma_in = nullptr;
+        o.eps_min = o.eps_max = 0.0;
+      }
+      refine_iter = it + 1;
+      a0 = it + 1;  // the new Anderson history holds only residuals of the refined arithmetic
+      since_best = 0;
+    }
+    if (so->mixer == SP2_MIX_LINEAR || (so->mixer == SP2_MIX_ANDERSON && it < a0)) {
       CK(launch_axpy_d(q, so->alpha, r, tot, h->stream));
       c.kernels++;
     } else if (so->mixer == SP2_MIX_ANDERSON) {
-      const int slot = it % m, me = it + 1 < m ? it + 1 : m;
+      const int ia = it - a0;
+      const int slot = ia % m, me = ia + 1 < m ? ia + 1 : m;
       CK(cudaMemcpyAsync(Qh + (size_t)slot * tot, q, tot * sizeof(double), cudaMemcpyDeviceToDevice,
                          h->stream));
       CK(cudaMemcpyAsync(Rh + (size_t)slot * tot, r, tot * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1597,6 +1641,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   if (info) {
     info->converged = done ? 1 : 0;
     info->M = 0;
+    info->refine_iter = refine_iter;
   }
   fill_timing(c, 1 << 30, info);
   if (!done) return fail(h, SP2_ENOCONV, "SCF residual above tol after %d iterations", so->max_iter);

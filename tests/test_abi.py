@@ -55,8 +55,8 @@ def test_nm_shows_c_linkage(lib):
 
 
 def test_struct_layout_matches_c(tmp_path, lib):
-    """sizeof/offsetof of sp2_opts and sp2_info from a C compiler agree with
-    the ctypes mirror used by the binding."""
+    """sizeof/offsetof of sp2_opts, sp2_info and sp2_scf_opts from a C compiler
+    agree with the ctypes mirror used by the binding."""
     gcc = shutil.which("gcc") or shutil.which("cc")
     if gcc is None:
         pytest.skip("no C compiler")
@@ -64,12 +64,15 @@ def test_struct_layout_matches_c(tmp_path, lib):
     probe = tmp_path / "probe.c"
     fields_o = [f for f, _ in _lib.Opts._fields_]
     fields_i = [f for f, _ in _lib.Info._fields_]
+    fields_s = [f for f, _ in _lib.ScfOpts._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){",
-             'printf("%zu %zu\\n", sizeof(sp2_opts), sizeof(sp2_info));']
+             'printf("%zu %zu %zu\\n", sizeof(sp2_opts), sizeof(sp2_info), sizeof(sp2_scf_opts));']
     for f in fields_o:
         lines.append(f'printf("%zu\\n", offsetof(sp2_opts, {f}));')
     for f in fields_i:
         lines.append(f'printf("%zu\\n", offsetof(sp2_info, {f}));')
+    for f in fields_s:
+        lines.append(f'printf("%zu\\n", offsetof(sp2_scf_opts, {f}));')
     lines.append("return 0;}")
     probe.write_text("\n".join(lines))
     exe = tmp_path / "probe"
@@ -78,11 +81,16 @@ def test_struct_layout_matches_c(tmp_path, lib):
                                            check=True).stdout.split()]
     assert vals[0] == C.sizeof(_lib.Opts)
     assert vals[1] == C.sizeof(_lib.Info)
-    offs = vals[2:]
-    for f, off in zip(fields_o, offs[:len(fields_o)]):
+    assert vals[2] == C.sizeof(_lib.ScfOpts)
+    offs = vals[3:]
+    no, ni = len(fields_o), len(fields_i)
+    for f, off in zip(fields_o, offs[:no]):
         assert getattr(_lib.Opts, f).offset == off, f
-    for f, off in zip(fields_i, offs[len(fields_o):]):
+    for f, off in zip(fields_i, offs[no:no + ni]):
         assert getattr(_lib.Info, f).offset == off, f
+    for f, off in zip(fields_s, offs[no + ni:]):
+        assert getattr(_lib.ScfOpts, f).offset == off, f
+    assert len(offs) == no + ni + len(fields_s)
 
 
 def test_default_opts_host_only(lib):

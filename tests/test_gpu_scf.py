@@ -62,6 +62,24 @@ def test_scf_split_precision(pkg, small):
     assert rel(q, scf.scf_exact(chi0, K, Vx)) < 1e-3
 
 
+def test_scf_precision_refinement(pkg, small):
+    """Split FP16X2 responses do the first iterations; below 1e-4 (or on a stall)
+    the loop switches to FP64 responses, whose own SP2 polynomial is converged
+    once and fixed, and reaches a residual the split arithmetic cannot (1e-10),
+    at the exact solution."""
+    tb, chi0, K, Vx = small
+    H = torch.from_numpy(tb.H).cuda()
+    q, res, its, _, info = pkg.sp2_scf_response(H, tb.nocc, 4, K, Vx, mixer="anderson", tol=1e-10,
+                                                max_iter=100, mode="fp16x2", refine_mode="fp64",
+                                                refine_below=1e-4, return_info=True)
+    assert res[-1] <= 1e-10
+    assert 0 < info["refine_iter"] < its
+    assert rel(q, scf.scf_exact(chi0, K, Vx)) < 1e-8
+    _, res16, _, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, Vx, mixer="anderson", tol=1e-10,
+                                          max_iter=40, mode="fp16x2", allow_noconv=True)
+    assert min(res16) > 1e-10                # the split arithmetic alone floors above it
+
+
 def test_mlp_kernels_against_oracle(pkg):
     rng = np.random.default_rng(0)
     din, dh, P = 96, 40, 70
@@ -108,11 +126,14 @@ def test_mlp_training_matches_oracle_adam(pkg):
     assert rel(W2g.cpu().numpy(), w2) < 1e-4
 
 
-def test_learned_preconditioner_reduces_iterations(pkg, small):
-    """Train the MLP on residual -> (q* - q - alpha r) pairs from linear-mixing
-    runs of training fields, then precondition held-out fields: fewer SCF
-    iterations than linear mixing to the same residual (judged by the plain
-    method)."""
+@pytest.mark.parametrize("a_mlp", [0.3, 1.0])
+def test_learned_preconditioner_reduces_iterations(pkg, small, a_mlp):
+    """Train the MLP on residual -> (q* - q - a r) pairs from linear-mixing
+    runs (step a) of training fields, then precondition held-out fields with
+    q <- q + a r + |r| MLP(r/|r|): fewer SCF iterations than linear mixing at
+    alpha = 0.3 to the same residual (judged by the plain method). a = 1 is the
+    form used at scale: the correction beyond a unit step, A (I - A)^-1 r for
+    A = chi0 K, lives on the few stiff modes of A."""
     tb, chi0, K, _ = small
     H = torch.from_numpy(tb.H).cuda()
     train = workloads.site_fields(tb, 96, seed=10)
@@ -120,10 +141,11 @@ def test_learned_preconditioner_reduces_iterations(pkg, small):
     tol = 1e-6
     q_star, _, _, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, train, mixer="anderson", tol=1e-10,
                                            max_iter=300, mode="fp64")
-    _, _, its, (tr, tq) = pkg.sp2_scf_response(H, tb.nocc, 4, K, train, mixer="linear", alpha=0.3,
-                                               tol=tol, max_iter=300, record=True, mode="fp64")
+    _, _, its, (tr, tq) = pkg.sp2_scf_response(H, tb.nocc, 4, K, train, mixer="linear", alpha=a_mlp,
+                                               tol=tol, max_iter=60, record=True, mode="fp64",
+                                               allow_noconv=True)
     R = tr.reshape(-1, tr.shape[-1]).cpu().numpy()
-    Tt = (torch.from_numpy(q_star).cuda()[None] - tq - 0.3 * tr).reshape(-1, tq.shape[-1]).cpu().numpy()
+    Tt = (torch.from_numpy(q_star).cuda()[None] - tq - a_mlp * tr).reshape(-1, tq.shape[-1]).cpu().numpy()
     nr = np.linalg.norm(R, axis=1, keepdims=True)
     keep = nr[:, 0] > 0
     Xn, Tn = R[keep] / nr[keep], Tt[keep] / nr[keep]
@@ -137,7 +159,7 @@ def test_learned_preconditioner_reduces_iterations(pkg, small):
     _, res_lin, it_lin, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, test, mixer="linear", alpha=0.3,
                                                  tol=tol, max_iter=300, mode="fp64")
     q_mlp, res_mlp, it_mlp, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, test, mixer="mlp", W1=W1,
-                                                     W2=W2, bf16_infer=True, tol=tol,
+                                                     W2=W2, bf16_infer=True, tol=tol, alpha=a_mlp,
                                                      max_iter=300, mode="fp64")
     assert res_mlp[-1] <= tol
     assert it_mlp < it_lin
