@@ -80,6 +80,24 @@ def test_scf_precision_refinement(pkg, small):
     assert min(res16) > 1e-10                # the split arithmetic alone floors above it
 
 
+def test_scf_dual_on_gpu(pkg, small):
+    """Eq. CP_SCF on the GPU: the response of the x, y, z site dipoles to 6
+    fields, primal (one SCF solve per field) against dual (one SCF solve per
+    observable, the observable as the field, then dot products), FP64, and
+    both against the oracle's exact solve."""
+    tb, chi0, K, Vx = small
+    H = torch.from_numpy(tb.H).cuda()
+    obs = np.ascontiguousarray((tb.pos - 0.5 * tb.box).T)
+    kw = dict(mixer="anderson", alpha=0.3, tol=1e-12, max_iter=300, mode="fp64", idem_tol=1e-13)
+    q_f, _, _, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, Vx, **kw)
+    q_a, _, _, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, obs, **kw)
+    primal = obs @ q_f.T
+    dual = q_a @ Vx.T
+    exact_ = obs @ scf.scf_exact(chi0, K, Vx).T
+    assert rel(dual, primal) < 1e-9
+    assert rel(primal, exact_) < 1e-8 and rel(dual, exact_) < 1e-8
+
+
 def test_mlp_kernels_against_oracle(pkg):
     rng = np.random.default_rng(0)
     din, dh, P = 96, 40, 70

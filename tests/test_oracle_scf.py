@@ -92,3 +92,21 @@ def test_adam_matches_definition():
     w1, m1, v1 = scf.adam_step(w, g, m, v, 1, 0.1)
     # first step: m_hat = g, v_hat = g^2 -> w - lr * g / (|g| + eps) = w - lr * sign(g)
     assert np.allclose(w1, w - 0.1 * np.sign(g), atol=1e-7)
+
+
+def test_scf_dual_equals_primal(small):
+    """Self-consistent duality (Eq. CP_SCF for the site-charge model): for a
+    site observable a and an external field V, a . q*(V) = q*(a) . V, because
+    (I - chi0 K)^(-1) chi0 = chi0 (I - K chi0)^(-1) is symmetric for symmetric
+    chi0 and K. One self-consistent solve per observable then gives the
+    response to every field. A solve with the transposed operator or the
+    factors in the other order breaks the identity."""
+    tb, e, V, chi0, K, Vx = small
+    ctr = tb.pos - 0.5 * tb.box
+    obs = ctr.T.copy()                                  # x, y, z site dipoles
+    primal = obs @ scf.scf_exact(chi0, K, Vx).T         # [l, k] = a_l . q*(V_k)
+    dual = scf.scf_exact(chi0, K, obs) @ Vx.T           # [l, k] = q*(a_l) . V_k
+    assert np.allclose(primal, dual, rtol=1e-10, atol=1e-12 * np.abs(primal).max())
+    # the non-self-consistent limit K = 0 is the plain symmetry of chi0
+    Z = np.zeros_like(K)
+    assert np.allclose(obs @ scf.scf_exact(chi0, Z, Vx).T, (obs @ chi0) @ Vx.T, rtol=1e-10)
