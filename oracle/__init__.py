@@ -22,7 +22,11 @@ Contents (each function cites the passage it follows):
                    eigenvalues (finite-M reference).
 * ``split``     -- the hi/lo half-precision splitting of Eq. doubleHalf and the
                    three-product mixed-precision multiplication of Eq. MixPrecMult
-                   with the lo*lo term dropped (Eq. mults).
+                   with the lo*lo term dropped (Eq. mults); the three-plane
+                   bfloat16 split and its six-term product (tunable accuracy).
+* ``fermi``     -- the finite-temperature recursion of Sec. V.B and its responses.
+* ``scf``       -- the site-charge self-consistent response (Appendix, Eq.
+                   DM_CP_SCF), its exact solve, mixers and the MLP.
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 a closed form, an invariant, brute force or a library routine (see

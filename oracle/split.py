@@ -64,3 +64,27 @@ def mixed_product(X: np.ndarray, Y: np.ndarray, kind: str = "bf16",
     yh, yl = split_hi_lo(Y, kind, lo_scale, sy)
     xh, xl, yh, yl = (a.astype(np.float64) for a in (xh, xl, yh, yl))
     return (xh @ yh + (xh @ yl + xl @ yh) / lo_scale) / (sx * sy)
+
+
+def split_hi_mid_lo(x: np.ndarray):
+    """Three bfloat16 planes of an FP32 value (the multi-split extension the
+    paper's Sec. VI.C points to for tunable accuracy): hi = bf16(x),
+    mid = bf16(x - hi), lo = bf16(x - hi - mid). Each residual is exact in
+    FP32 and each plane carries the next 8 significand bits, so
+    hi + mid + lo = x exactly for normal FP32 x (bfloat16 shares FP32's
+    exponent range; only residuals below the smallest normal lose bits)."""
+    x32 = np.asarray(x, dtype=np.float32)
+    hi = round_bf16(x32)
+    r1 = x32 - hi
+    mid = round_bf16(r1)
+    lo = round_bf16(r1 - mid)
+    return hi, mid, lo
+
+
+def mixed_product3(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Product of the three-plane splits keeping every term down to 2^-16
+    relative (hi.hi; hi.mid, mid.hi; hi.lo, mid.mid, lo.hi) and dropping the
+    2^-24 and 2^-32 ones (mid.lo, lo.mid, lo.lo), in FP64."""
+    xh, xm, xl = (a.astype(np.float64) for a in split_hi_mid_lo(X))
+    yh, ym, yl = (a.astype(np.float64) for a in split_hi_mid_lo(Y))
+    return xh @ yh + (xh @ ym + xm @ yh) + (xh @ yl + xm @ ym + xl @ yh)

@@ -169,3 +169,34 @@ def test_scaled_fp16_split_product():
     P = split.mixed_product(Y, X, "fp16", lo_scale=2048.0, sx=s)
     assert np.isfinite(P).all()
     assert np.linalg.norm(P - Y @ X) / np.linalg.norm(Y @ X) < 1e-6
+
+
+def test_three_plane_split_is_exact_and_ordered():
+    """hi + mid + lo reconstructs FP32 exactly; each plane is a bfloat16 value
+    at most 2^-8 of the previous residual (relative to x: mid <= 2^-8 |x|,
+    lo <= 2^-16 |x|, up to the rounding of each step)."""
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    h, m, lo = split.split_hi_mid_lo(x)
+    for p in (h, m, lo):
+        assert np.array_equal(p, split.round_bf16(p))          # representable in bf16
+    assert np.array_equal((h.astype(np.float64) + m + lo).astype(np.float32), x)
+    assert np.array_equal(h.astype(np.float64) + m + lo, x.astype(np.float64))
+    ax = np.abs(x.astype(np.float64))
+    assert np.all(np.abs(m) <= 2.0 ** -8 * ax * (1 + 2.0 ** -7))
+    assert np.all(np.abs(lo) <= 2.0 ** -16 * ax * (1 + 2.0 ** -6))
+
+
+def test_three_plane_product_accuracy():
+    """The six-term product is within a few 2^-24 of the exact FP32-input
+    product (the dropped terms are 2^-24 relative per element pair), far below
+    the two-plane form's 2^-16."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((96, 96)).astype(np.float32)
+    Y = rng.standard_normal((96, 96)).astype(np.float32)
+    exact_ = X.astype(np.float64) @ Y.astype(np.float64)
+    scale = np.abs(X).astype(np.float64) @ np.abs(Y).astype(np.float64)
+    e3 = np.max(np.abs(split.mixed_product3(X, Y) - exact_) / scale)
+    e2 = np.max(np.abs(split.mixed_product(X, Y, "bf16") - exact_) / scale)
+    assert e3 < 4 * 2.0 ** -24
+    assert e2 > 16 * e3
