@@ -85,12 +85,19 @@ typedef enum { SP2_F64 = 0, SP2_F32 = 1 } sp2_dtype;
  *                    plane holds the residual times 2^11 and is accumulated
  *                    separately; response matrices carry a per-matrix
  *                    power-of-two scale so that no plane entry exceeds 2^14.
+ *   SP2_MODE_BF16X3  three bfloat16 planes hi + mid + lo (exact for FP32 values)
+ *                    and six tensor-core products keeping every term down to
+ *                    2^-16 relative (hi*hi; hi*mid, mid*hi; hi*lo, mid*mid,
+ *                    lo*hi): the multi-split extension of Eq. MixPrecMult
+ *                    that Sec. VI.C names for tunable accuracy; twice the
+ *                    tensor work of the two-plane modes, no scaling.
  */
 typedef enum {
   SP2_MODE_FP64 = 0,
   SP2_MODE_FP32 = 1,
   SP2_MODE_BF16X2 = 2,
-  SP2_MODE_FP16X2 = 3
+  SP2_MODE_FP16X2 = 3,
+  SP2_MODE_BF16X3 = 4
 } sp2_mode;
 
 typedef struct {

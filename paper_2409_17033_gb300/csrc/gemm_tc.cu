@@ -8,6 +8,9 @@
 // into FP32 accumulators in tensor memory. X is symmetric, so the row-major
 // X planes are directly the K-major B operand.
 //   BF16X2: one accumulator for all three segments.
+//   BF16X3: three bfloat16 planes (hi + mid + lo = the FP32 value) and six
+//           segments [A_h|A_h|A_m|A_h|A_m|A_l] . [X_h;X_m;X_h;X_l;X_m;X_h]: every
+//           term down to 2^-16 relative, K = 6 np, no scaling.
 //   FP16X2: the lo planes hold residuals times 2^11, so segment 0 (hi*hi) and
 //           segments 1-2 (hi*lo, lo*hi) go to two accumulators (512 TMEM
 //           columns) combined as acc0 + 2^-11 acc1; A may carry a per-matrix
@@ -174,32 +177,48 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <bool F16>
-__device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* lo, int64_t idx, float v) {
+// plane kinds of the product kernel
+constexpr int KIND_BF16X2 = 0, KIND_FP16X2 = 1, KIND_BF16X3 = 2;
+
+template <int KIND>
+__device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* mid, uint16_t* lo, int64_t idx,
+                                            float v) {
   uint16_t h, l;
-  if (F16) split_fp16(v, 1.0f, h, l);
-  else split_bf16(v, h, l);
+  if constexpr (KIND == KIND_FP16X2) {
+    split_fp16(v, 1.0f, h, l);
+  } else if constexpr (KIND == KIND_BF16X3) {
+    uint16_t m;
+    split_bf16x3(v, h, m, l);
+    mid[idx] = m;
+  } else {
+    split_bf16(v, h, l);
+  }
   hi[idx] = h;
   lo[idx] = l;
 }
 
-template <bool F16>
-__device__ __forceinline__ void store_split(float* m, uint16_t* hi, uint16_t* lo, int64_t idx,
-                                            float v) {
+template <int KIND>
+__device__ __forceinline__ void store_split(float* m, uint16_t* hi, uint16_t* mid, uint16_t* lo,
+                                            int64_t idx, float v) {
   m[idx] = v;
-  split_store<F16>(hi, lo, idx, v);
+  split_store<KIND>(hi, mid, lo, idx, v);
 }
 
-template <bool F16>
+template <int KIND>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
           const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+          const __grid_constant__ CUtensorMap mA_mid, const __grid_constant__ CUtensorMap mB_mid,
           int nkb, int ch, int epi, int64_t np, float* __restrict__ out,
           uint16_t* __restrict__ out_hi, uint16_t* __restrict__ out_lo,
+          uint16_t* __restrict__ out_mid,
           const float* __restrict__ xprev, Part3* __restrict__ part,
           const Tile* __restrict__ tiles, int ntiles, DevState* st, int step,
           const float* __restrict__ a_scale, const float* __restrict__ b_scale,
           float* __restrict__ zmax) {
+  constexpr bool F16 = KIND == KIND_FP16X2;
+  constexpr bool X3 = KIND == KIND_BF16X3;
+  constexpr int NSEG = X3 ? 6 : 3;
   constexpr uint32_t kIdesc = idesc_for(F16);
   {
     const int m = *((volatile const int*)&st->stop_at);
@@ -217,7 +236,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* abortf = &st->abort_flag;
-  const int total_kb = 3 * nkb;
+  const int total_kb = NSEG * nkb;
   const int nchunks = total_kb / ch;
   // persistent static schedule: this CTA handles tiles blockIdx.x, +gridDim.x, ...
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -264,8 +283,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
           }
           const int seg = kb / nkb;
           const int kx = (kb - seg * nkb) * BK;
-          const CUtensorMap* ma = seg < 2 ? &mA_hi : &mA_lo;
-          const CUtensorMap* mb = seg == 1 ? &mB_lo : &mB_hi;
+          const CUtensorMap* ma;
+          const CUtensorMap* mb;
+          if constexpr (X3) {
+            // segments hh, hm, mh, hl, mm, lh
+            ma = (seg == 2 || seg == 4) ? &mA_mid : (seg == 5 ? &mA_lo : &mA_hi);
+            mb = (seg == 1 || seg == 4) ? &mB_mid : (seg == 3 ? &mB_lo : &mB_hi);
+          } else {
+            ma = seg < 2 ? &mA_hi : &mA_lo;
+            mb = seg == 1 ? &mB_lo : &mB_hi;
+          }
           uint8_t* sa = smem + s * STAGE_BYTES;
           mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
           tma_load_2d(ma, &full[s], sa, kx, t.row0);
@@ -418,10 +445,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
           for (int j = 0; j < 4; ++j)
             dm[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
           __align__(16) uint16_t hh[16], ll[16];
+          if constexpr (X3) {
+            __align__(16) uint16_t mm[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (F16) split_fp16(val[j], 1.0f, hh[j], ll[j]);
-            else split_bf16(val[j], hh[j], ll[j]);
+            for (int j = 0; j < 16; ++j) split_bf16x3(val[j], hh[j], mm[j], ll[j]);
+            uint4* dmid = reinterpret_cast<uint4*>(out_mid + gi * np + gj0);
+            dmid[0] = reinterpret_cast<const uint4*>(mm)[0];
+            dmid[1] = reinterpret_cast<const uint4*>(mm)[1];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (F16) split_fp16(val[j], 1.0f, hh[j], ll[j]);
+              else split_bf16(val[j], hh[j], ll[j]);
+            }
           }
           uint4* dh = reinterpret_cast<uint4*>(out_hi + gi * np + gj0);
           uint4* dl = reinterpret_cast<uint4*>(out_lo + gi * np + gj0);
@@ -432,7 +468,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (gj0 + j >= gi) store_split<F16>(out, out_hi, out_lo, gi * np + gj0 + j, val[j]);
+            if (gj0 + j >= gi)
+              store_split<KIND>(out, out_hi, out_mid, out_lo, gi * np + gj0 + j, val[j]);
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -444,7 +481,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
             t2 = fmaf(d, d, t2);
             f = fmaf(rr, rr, f);
           } else {
-            store_split<F16>(out, out_hi, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
+            store_split<KIND>(out, out_hi, out_mid, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
             t2 = fmaf(2.0f * d, d, t2);
             f = fmaf(2.0f * rr, rr, f);
           }
@@ -539,27 +576,43 @@ cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t 
                            DevState* st, int step, const float* a_scale, float* zmax,
                            cudaStream_t s, char* errbuf, size_t errlen, const float* b_scale) {
   if (ntiles <= 0) return cudaSuccess;
-  const bool f16 = mode == SP2_MODE_FP16X2;
-  static bool attr_done[2] = {false, false};
-  if (!attr_done[f16]) {
-    cudaError_t e = f16 ? cudaFuncSetAttribute(k_gemm_tc<true>,
+  const int kind = mode == SP2_MODE_FP16X2 ? KIND_FP16X2
+                                           : (mode == SP2_MODE_BF16X3 ? KIND_BF16X3 : KIND_BF16X2);
+  const bool f16 = kind == KIND_FP16X2, x3 = kind == KIND_BF16X3;
+  static bool attr_done[3] = {false, false, false};
+  if (!attr_done[kind]) {
+    cudaError_t e = kind == KIND_FP16X2
+                        ? cudaFuncSetAttribute(k_gemm_tc<KIND_FP16X2>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
-                        : cudaFuncSetAttribute(k_gemm_tc<false>,
+                    : kind == KIND_BF16X3
+                        ? cudaFuncSetAttribute(k_gemm_tc<KIND_BF16X3>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
+                        : cudaFuncSetAttribute(k_gemm_tc<KIND_BF16X2>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_done[f16] = true;
+    attr_done[kind] = true;
+  }
+  // the middle planes exist only in BF16X3; elsewhere the hi maps stand in (never read)
+  const uint16_t* a_mid = x3 ? A.mid : A.hi;
+  const uint16_t* b_mid = x3 ? B.mid : B.hi;
+  if (x3 && (!a_mid || !b_mid || (epi == EPI_SQUARE && !out.mid))) {
+    snprintf(errbuf, errlen, "tcgen05 product: BF16X3 operand without its middle plane");
+    return cudaErrorInvalidValue;
   }
   // TMA box/stride rules: 16-byte aligned bases, np*2-byte row pitch (np % 256 == 0),
   // every x coordinate a multiple of 64 elements.
   if ((reinterpret_cast<uintptr_t>(A.hi) | reinterpret_cast<uintptr_t>(A.lo) |
-       reinterpret_cast<uintptr_t>(B.hi) | reinterpret_cast<uintptr_t>(B.lo)) & 15u ||
+       reinterpret_cast<uintptr_t>(B.hi) | reinterpret_cast<uintptr_t>(B.lo) |
+       reinterpret_cast<uintptr_t>(a_mid) | reinterpret_cast<uintptr_t>(b_mid)) & 15u ||
       np % 256 != 0 || A.rows % BM != 0 || B.rows % BN != 0) {
     snprintf(errbuf, errlen, "tcgen05 product: operand alignment/shape violates the TMA rules");
     return cudaErrorInvalidValue;
   }
-  CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
+  CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid;
   if (!make_map(&ma_hi, A.hi, A.rows, np, BM, f16) || !make_map(&ma_lo, A.lo, A.rows, np, BM, f16) ||
-      !make_map(&mb_hi, B.hi, B.rows, np, BN, f16) || !make_map(&mb_lo, B.lo, B.rows, np, BN, f16)) {
+      !make_map(&mb_hi, B.hi, B.rows, np, BN, f16) || !make_map(&mb_lo, B.lo, B.rows, np, BN, f16) ||
+      !make_map(&ma_mid, a_mid, A.rows, np, BM, f16) ||
+      !make_map(&mb_mid, b_mid, B.rows, np, BN, f16)) {
     snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     return cudaErrorInvalidValue;
   }
@@ -581,14 +634,19 @@ cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t 
       nsm = 1;
   }
   const int grid = ntiles < nsm ? ntiles : nsm;
-  if (f16)
-    k_gemm_tc<true><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
-        out.lo, x_prev, part, tiles, ntiles, st, step, a_scale, b_scale, zmax);
+  float* om = static_cast<float*>(out.master);
+  if (kind == KIND_FP16X2)
+    k_gemm_tc<KIND_FP16X2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
+        ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid, nkb, ch, epi, np, om, out.hi, out.lo, out.mid,
+        x_prev, part, tiles, ntiles, st, step, a_scale, b_scale, zmax);
+  else if (kind == KIND_BF16X3)
+    k_gemm_tc<KIND_BF16X3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
+        ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid, nkb, ch, epi, np, om, out.hi, out.lo, out.mid,
+        x_prev, part, tiles, ntiles, st, step, nullptr, nullptr, nullptr);
   else
-    k_gemm_tc<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, nkb, ch, epi, np, static_cast<float*>(out.master), out.hi,
-        out.lo, x_prev, part, tiles, ntiles, st, step, nullptr, nullptr, nullptr);
+    k_gemm_tc<KIND_BF16X2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
+        ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid, nkb, ch, epi, np, om, out.hi, out.lo, out.mid,
+        x_prev, part, tiles, ntiles, st, step, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

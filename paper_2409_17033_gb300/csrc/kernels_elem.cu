@@ -111,6 +111,12 @@ __device__ __forceinline__ void store_elem(MatBuf d, int mode, int64_t idx, doub
     split_fp16(f, 1.0f, h, l);
     d.hi[idx] = h;
     d.lo[idx] = l;
+  } else if (mode == SP2_MODE_BF16X3) {
+    uint16_t m;
+    split_bf16x3(f, h, m, l);
+    d.hi[idx] = h;
+    d.mid[idx] = m;
+    d.lo[idx] = l;
   }
 }
 
@@ -257,6 +263,17 @@ __device__ __forceinline__ void store_y4(MatBuf y, int64_t idx, const ZT (&v)[4]
     d[0] = make_double2((double)v[0], (double)v[1]);
     d[1] = make_double2((double)v[2], (double)v[3]);
   }
+  if (MODE == SP2_MODE_BF16X3) {
+    uint16_t h[4], m[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) split_bf16x3((float)v[j], h[j], m[j], l[j]);
+    *reinterpret_cast<uint2*>(y.hi + idx) =
+        make_uint2(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16));
+    *reinterpret_cast<uint2*>(y.mid + idx) =
+        make_uint2(m[0] | ((uint32_t)m[1] << 16), m[2] | ((uint32_t)m[3] << 16));
+    *reinterpret_cast<uint2*>(y.lo + idx) =
+        make_uint2(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16));
+  }
   if (MODE == SP2_MODE_BF16X2 || MODE == SP2_MODE_FP16X2) {
     uint16_t h[4], l[4];
 #pragma unroll
@@ -368,8 +385,15 @@ __global__ void k_split(MatBuf m, int64_t total, int mode) {
        t += (int64_t)gridDim.x * blockDim.x) {
     const float f = static_cast<const float*>(m.master)[t];
     uint16_t h, l;
-    if (mode == SP2_MODE_BF16X2) split_bf16(f, h, l);
-    else split_fp16(f, 1.0f, h, l);
+    if (mode == SP2_MODE_BF16X3) {
+      uint16_t md;
+      split_bf16x3(f, h, md, l);
+      m.mid[t] = md;
+    } else if (mode == SP2_MODE_BF16X2) {
+      split_bf16(f, h, l);
+    } else {
+      split_fp16(f, 1.0f, h, l);
+    }
     m.hi[t] = h;
     m.lo[t] = l;
   }
@@ -480,6 +504,9 @@ cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t
         static_cast<const float*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
   else if (mode == SP2_MODE_BF16X2)
     k_symm_update<float, SP2_MODE_BF16X2><<<grid, block, 0, s>>>(
+        static_cast<const float*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
+  else if (mode == SP2_MODE_BF16X3)
+    k_symm_update<float, SP2_MODE_BF16X3><<<grid, block, 0, s>>>(
         static_cast<const float*>(Z), y_in, y_out, np, st, step, sc, slot_in, slot_out);
   else
     k_symm_update<float, SP2_MODE_FP16X2><<<grid, block, 0, s>>>(

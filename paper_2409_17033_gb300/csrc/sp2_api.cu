@@ -125,6 +125,10 @@ int mat(sp2_handle_t h, const std::string& name, int64_t rows, int64_t np, int m
     m->hi = static_cast<uint16_t*>(p);
     TRY(ws(h, name + ".l", cnt * 2, &p));
     m->lo = static_cast<uint16_t*>(p);
+    if (n_planes(mode) == 3) {
+      TRY(ws(h, name + ".d", cnt * 2, &p));
+      m->mid = static_cast<uint16_t*>(p);
+    }
   }
   return SP2_OK;
 }
@@ -281,7 +285,8 @@ int64_t timed_count(const Ctx& c, int m) {
   return k;
 }
 
-double k_mult(int mode) { return split_mode(mode) ? 3.0 : 1.0; }
+// tensor products per logical product: 3 (two planes), 6 (BF16X3), 1 (plain)
+double k_mult(int mode) { return n_planes(mode) == 3 ? 6.0 : (split_mode(mode) ? 3.0 : 1.0); }
 
 // X_{n+1} = sigma_n>0 ? X_n^2 : 2 X_n - X_n^2, with trace partials; returns #partials
 int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* nparts) {
@@ -298,7 +303,7 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   }
   if (split_mode(c.mode)) {
     char eb[256] = {0};
-    TcOperand a{xin.hi, xin.lo, c.np};
+    TcOperand a{xin.hi, xin.lo, c.np, xin.mid};
     cudaError_t e = launch_gemm_tc(c.mode, EPI_SQUARE, a, a, c.np, xout,
                                    static_cast<const float*>(xin.master), c.part, tl, nt, c.st,
                                    step, nullptr, nullptr, h->stream, eb, sizeof eb);
@@ -340,7 +345,7 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
   if (f16) CK(cudaMemsetAsync(sc.zmax, 0, sizeof(float) * batch, h->stream));
   if (split_mode(c.mode)) {
     char eb[256] = {0};
-    TcOperand a{yin.hi, yin.lo, rows}, b{x.hi, x.lo, c.np};
+    TcOperand a{yin.hi, yin.lo, rows, yin.mid}, b{x.hi, x.lo, c.np, x.mid};
     MatBuf zo;
     zo.master = z;
     cudaError_t e = launch_gemm_tc(c.mode, EPI_PLAIN, a, b, c.np, zo, nullptr, c.part, tl, nt, c.st,
@@ -367,7 +372,7 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
 
 // With every X_n kept (k = 1) in a split mode, the checkpoint holds the hi/lo planes
 // (np^2 x 4 bytes, the size of the FP32 master) instead of the master.
-bool ckpt_planes(int mode, int k) { return k == 1 && split_mode(mode); }
+bool ckpt_planes(int mode, int k) { return k == 1 && n_planes(mode) == 2; }
 
 // SP2_CKPT_AUTO: the smallest checkpoint interval k whose kept history fits in device
 // memory next to the working set, so X_n is recomputed only when the history of
@@ -380,7 +385,7 @@ int resolve_ckpt(sp2_handle_t h, sp2_opts* o, int64_t np, int64_t batch) {
   double avail = (double)fr;
   if (h->limit) avail = std::min(avail, (double)h->limit - (double)h->held);
   const double el = (double)np * (double)np;
-  const double ms = (double)master_size(o->mode), mat_b = el * (ms + (split_mode(o->mode) ? 4 : 0));
+  const double ms = (double)master_size(o->mode), mat_b = el * (ms + 2.0 * n_planes(o->mode));
   const double b = (double)(batch > 0 ? batch : 1);
   avail -= 2.0 * mat_b + 2.0 * b * mat_b + b * el * ms + (double)(1ull << 30);
   const int cap = o->fixed_m > 0 ? o->fixed_m : o->max_iter;
@@ -398,7 +403,7 @@ int resolve_ckpt(sp2_handle_t h, sp2_opts* o, int64_t np, int64_t batch) {
 
 int validate_opts(sp2_handle_t h, const sp2_opts* o) {
   if (o->mode != SP2_MODE_FP64 && o->mode != SP2_MODE_FP32 && o->mode != SP2_MODE_BF16X2 &&
-      o->mode != SP2_MODE_FP16X2)
+      o->mode != SP2_MODE_FP16X2 && o->mode != SP2_MODE_BF16X3)
     return fail(h, SP2_EINVAL, "unknown mode %d", o->mode);
   if (o->max_iter < 1 || o->max_iter > SP2_MAX_ITER)
     return fail(h, SP2_EINVAL, "max_iter %d outside 1..%d", o->max_iter, SP2_MAX_ITER);
@@ -686,6 +691,10 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
     seg[0].hi = static_cast<uint16_t*>(p);
     TRY(ws(h, "seg.0.l", (size_t)np * np * 2, &p));
     seg[0].lo = static_cast<uint16_t*>(p);
+    if (n_planes(mode) == 3) {
+      TRY(ws(h, "seg.0.d", (size_t)np * np * 2, &p));
+      seg[0].mid = static_cast<uint16_t*>(p);
+    }
   }
   const size_t xbytes = (size_t)np * np * master_size(mode);
   const int nseg = (M + k - 1) / k;
@@ -745,7 +754,7 @@ int fmat(sp2_handle_t h, const std::string& name, int64_t np, int mode, FMat* f)
 // hi/lo planes of f from its master (FP16X2: scale from f->amax)
 int fplanes(Ctx& c, FMat& f) {
   sp2_handle_t h = c.h;
-  if (c.mode == SP2_MODE_BF16X2) {
+  if (c.mode == SP2_MODE_BF16X2 || c.mode == SP2_MODE_BF16X3) {
     CK(launch_split(f.m, c.np, c.np, c.mode, h->stream));
     c.kernels++;
   } else if (c.mode == SP2_MODE_FP16X2) {
@@ -777,7 +786,7 @@ int fprod(Ctx& c, FMat& C, const FMat& L, const FMat& R) {
     const bool f16 = c.mode == SP2_MODE_FP16X2;
     if (f16) CK(cudaMemsetAsync(C.amax, 0, sizeof(float), h->stream));
     char eb[256] = {0};
-    TcOperand a{L.m.hi, L.m.lo, c.np}, b{R.m.hi, R.m.lo, c.np};
+    TcOperand a{L.m.hi, L.m.lo, c.np, L.m.mid}, b{R.m.hi, R.m.lo, c.np, R.m.mid};
     cudaError_t e = launch_gemm_tc(c.mode, EPI_PLAIN, a, b, c.np, C.m, nullptr, c.part, tl, nt,
                                    c.st, 0, f16 ? L.scale : nullptr, f16 ? C.amax : nullptr,
                                    h->stream, eb, sizeof eb, f16 ? R.scale : nullptr);
@@ -1480,7 +1489,8 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   TRY(validate_opts(h, &o));
   const bool refine = so->refine_below > 0.0 && so->refine_mode != o.mode;
   if (refine && so->refine_mode != SP2_MODE_FP64 && so->refine_mode != SP2_MODE_FP32 &&
-      so->refine_mode != SP2_MODE_BF16X2 && so->refine_mode != SP2_MODE_FP16X2)
+      so->refine_mode != SP2_MODE_BF16X2 && so->refine_mode != SP2_MODE_FP16X2 &&
+      so->refine_mode != SP2_MODE_BF16X3)
     return fail(h, SP2_EINVAL, "unknown refine_mode %d", so->refine_mode);
   if (info) memset(info, 0, sizeof *info);
   const int64_t ns = N / norb, np = pad_n(N), tot = F * ns;

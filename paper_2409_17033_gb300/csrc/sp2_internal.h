@@ -38,15 +38,31 @@ struct MatBuf {
   void* master = nullptr;        // double (FP64 mode) or float, rows x np, unscaled
   uint16_t* hi = nullptr;        // split modes: hi plane (bf16 or fp16 bits)
   uint16_t* lo = nullptr;        // split modes: lo plane
+  uint16_t* mid = nullptr;       // BF16X3: the middle plane
 };
 
-inline bool split_mode(int mode) { return mode == SP2_MODE_BF16X2 || mode == SP2_MODE_FP16X2; }
+inline bool split_mode(int mode) {
+  return mode == SP2_MODE_BF16X2 || mode == SP2_MODE_FP16X2 || mode == SP2_MODE_BF16X3;
+}
+inline int n_planes(int mode) { return mode == SP2_MODE_BF16X3 ? 3 : (split_mode(mode) ? 2 : 0); }
 
 // Eq. doubleHalf with bfloat16: hi = bf16(v), lo = bf16(v - hi).
 __device__ __forceinline__ void split_bf16(float v, uint16_t& h, uint16_t& l) {
   const __nv_bfloat16 hb = __float2bfloat16_rn(v);
   const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
   h = __bfloat16_as_ushort(hb);
+  l = __bfloat16_as_ushort(lb);
+}
+
+// Three bfloat16 planes of v: hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid).
+// Both residuals are exact in FP32, so hi + mid + lo = v for normal v.
+__device__ __forceinline__ void split_bf16x3(float v, uint16_t& h, uint16_t& m, uint16_t& l) {
+  const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(hb);
+  const __nv_bfloat16 mb = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 lb = __float2bfloat16_rn(r1 - __bfloat162float(mb));
+  h = __bfloat16_as_ushort(hb);
+  m = __bfloat16_as_ushort(mb);
   l = __bfloat16_as_ushort(lb);
 }
 
@@ -158,10 +174,11 @@ cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, c
 void simt_tile_shape(int mode, int* bm, int* bn);
 
 // tcgen05 split-precision (BF16X2 / FP16X2)
-struct TcOperand {   // hi/lo planes of a stacked operand, rows x np
+struct TcOperand {   // hi/lo (and BF16X3 mid) planes of a stacked operand, rows x np
   const uint16_t* hi;
   const uint16_t* lo;
   int64_t rows;
+  const uint16_t* mid = nullptr;
 };
 // a_scale (FP16X2, EPI_PLAIN): per batch entry of A, the plane scale to divide
 // out; b_scale (FP16X2, nullable): the plane scale of B; zmax (FP16X2,

@@ -58,11 +58,12 @@ BOUNDS = {
     "fp32": (1e-4, 0.4, 0.25),       # measured 3.6e-5, 1.4e-1, 8.3e-2
     "fp16x2": (3e-5, 0.3, 0.2),      # measured 1.0e-5, 9.6e-2, 5.7e-2
     "bf16x2": (3e-2, None, None),    # measured 1.1e-2, 5.0, 4.5
+    "bf16x3": (3e-5, 0.3, 0.2),      # measured 1.1e-5, 9.6e-2, 5.7e-2 (three planes, six products)
 }
 ERRS = {}
 
 
-@pytest.mark.parametrize("mode", ["fp32", "fp16x2", "bf16x2"])
+@pytest.mark.parametrize("mode", ["fp32", "fp16x2", "bf16x2", "bf16x3"])
 def test_mode_against_exact(pkg, ref, mode):
     tb, A, v, D_ex, chi_ex, a1_ex, gap = ref
     H = torch.from_numpy(tb.H).cuda()

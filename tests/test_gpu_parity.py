@@ -95,7 +95,7 @@ def test_fp64_backward_checkpoint_segments(sp2, c1, k):
     assert rel(host(chi_b[0]), ref) < 1e-10
 
 
-@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2", "fp32"])
+@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2", "bf16x3", "fp32"])
 def test_checkpoint_policies_agree_bitwise(sp2, c1, mode):
     """Keeping every X_n (split modes: its hi/lo planes), every 3rd with segment
     recompute, and the memory-sized automatic choice run the same products on
@@ -210,6 +210,30 @@ def test_fp16x2_single_steps_match_emulated_split(sp2, c1):
         assert rel(host(chi[0]), ref) < 1e-6
 
 
+def test_bf16x3_single_steps_match_emulated_split(sp2, c1):
+    """BF16X3: one square step and one response step against the six-term
+    product of the three-plane split (hi + mid + lo) evaluated in FP64. What
+    remains is the FP32 accumulation, which the 256-wide chunks keep near the
+    FP32 rounding of the result."""
+    p, _ = c1
+    H = cuda(p.H, torch.float32)
+    for s in (1, -1):
+        D, info = sp2.sp2_density(H, p.nocc, mode="bf16x3", sigma=[s])
+        a, b = info["alpha"], info["beta"]
+        X1 = (a * np.eye(128) + b * p.H.astype(np.float32).astype(np.float64)).astype(np.float32)
+        P = split.mixed_product3(X1, X1)
+        ref = P if s > 0 else 2.0 * X1.astype(np.float64) - P
+        assert rel(host(D), ref) < 1e-6
+        assert np.array_equal(host(D), host(D).T)
+        chi, _, _ = sp2.sp2_susceptibility(H, p.nocc, cuda(p.A[None], torch.float32), "forward",
+                                           mode="bf16x3", sigma=[s])
+        Y1 = (b * p.A.astype(np.float32).astype(np.float64)).astype(np.float32)
+        Z = split.mixed_product3(Y1, X1)
+        Pz = Z + Z.T
+        ref = Pz if s > 0 else 2.0 * Y1.astype(np.float64) - Pz
+        assert rel(host(chi[0]), ref) < 1e-6
+
+
 def test_fp16x2_large_response_entries_do_not_overflow(sp2, c1):
     """Observables with entries far beyond the FP16 range (1e6) still give the
     exact response up to the split precision (per-matrix plane scales)."""
@@ -223,7 +247,7 @@ def test_fp16x2_large_response_entries_do_not_overflow(sp2, c1):
     assert rel(c, exact.response_zero_T(p.e, p.Q, p.nocc, A)) < 1e-3
 
 
-@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2"])
+@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2", "bf16x3"])
 def test_split_modes_converged_against_closed_forms(sp2, c1, mode):
     p, _ = c1
     H = cuda(p.H, torch.float32)
@@ -262,7 +286,7 @@ def test_bf16x2_converged_against_closed_forms(sp2, c1):
 
 # ------------------------------------------------------------------ ragged sizes / edges
 @pytest.mark.parametrize("n", [1, 17, 130, 300])
-@pytest.mark.parametrize("mode", ["fp64", "bf16x2", "fp16x2"])
+@pytest.mark.parametrize("mode", ["fp64", "bf16x2", "fp16x2", "bf16x3"])
 def test_ragged_sizes(sp2, n, mode):
     nocc = max(1, n // 3) if n > 1 else 1
     p = workloads.random_spectrum(n, nocc=nocc, k=1, seed=n)
@@ -270,7 +294,8 @@ def test_ragged_sizes(sp2, n, mode):
     chi, D, info = sp2.sp2_susceptibility(cuda(p.H, dt), p.nocc, cuda(p.A[None], dt), "backward",
                                           mode=mode, want_density=True,
                                           idem_tol=1e-10 if mode == "fp64" else 0.0)
-    tolD, tolC = {"fp64": (1e-10, 1e-8), "bf16x2": (1e-4, 1e-2), "fp16x2": (3e-5, 1e-3)}[mode]
+    tolD, tolC = {"fp64": (1e-10, 1e-8), "bf16x2": (1e-4, 1e-2), "fp16x2": (3e-5, 1e-3),
+                  "bf16x3": (3e-5, 1e-3)}[mode]
     assert rel(host(D), exact.density_zero_T(p.e, p.Q, p.nocc)) < tolD
     chi_ex = exact.response_zero_T(p.e, p.Q, p.nocc, p.A)
     if np.linalg.norm(chi_ex) > 0:
