@@ -27,9 +27,12 @@ Contents (each function cites the passage it follows):
 * ``fermi``     -- the finite-temperature recursion of Sec. V.B and its responses.
 * ``scf``       -- the site-charge self-consistent response (Appendix, Eq.
                    DM_CP_SCF), its exact solve, mixers and the MLP.
+* ``nonorth``   -- non-orthonormal representations (Sec. V.A): Loewdin factor,
+                   congruences, and the dual three-contraction form of the
+                   basis-set dependent derivative (Eq. NonOrthDer).
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 a closed form, an invariant, brute force or a library routine (see
 ``tests/test_oracle_*.py``). None is marked "parity unpinned".
 """
-from . import exact, fermi, scf, sp2, split  # noqa: F401
+from . import exact, fermi, nonorth, scf, sp2, split  # noqa: F401

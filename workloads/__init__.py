@@ -21,6 +21,9 @@ observables A are real symmetric N x N matrices, Sec. III and IV):
   alternating +/-0.8 shift that opens a gap at half filling.
 * ``metallic_spectrum``: H = Q diag(e) Q^T with e ~ U[-1, 1] (gapless), for
   the finite-temperature variant.
+* ``nonorth_problem``: an overlap S = L L^T from a drawn unit lower-triangular
+  L and H = L (Q diag(e) Q^T) L^T, so the generalized spectrum of (H, S) is the
+  gapped e; observable and basis-set dependent perturbations (A_t, H_t, S_t).
 """
 from __future__ import annotations
 
@@ -39,6 +42,8 @@ __all__ = [
     "tb_dipole_observables",
     "tb_site_potentials",
     "metallic_spectrum",
+    "NonOrthProblem",
+    "nonorth_problem",
 ]
 
 
@@ -207,3 +212,47 @@ def site_fields(tb: TightBinding, f: int, sigma: float = 0.1, seed: int = 2) -> 
     Draw order: F * n_sites normals, row-major."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((f, tb.n // tb.norb)) * sigma
+
+
+@dataclasses.dataclass
+class NonOrthProblem:
+    H: np.ndarray          # (N, N) symmetric, atomic-orbital representation
+    S: np.ndarray          # (N, N) symmetric positive definite overlap
+    A: np.ndarray          # (N, N) observable
+    A_t: np.ndarray        # (K, N, N) derivatives of A along K perturbations
+    H_t: np.ndarray        # (K, N, N) derivatives of H
+    S_t: np.ndarray        # (K, N, N) derivatives of S
+    e: np.ndarray          # (N,) generalized eigenvalues of (H, S)
+    nocc: int
+
+
+def nonorth_problem(n: int = 128, nocc: int | None = None, k: int = 3, overlap: float = 0.5,
+                    seed: int = 0) -> NonOrthProblem:
+    """Gapped generalized problem with a non-trivial overlap.
+
+    Draw order: Q (n*n normals), nocc eigenvalues U[-1, -0.2], n - nocc
+    eigenvalues U[0.2, 1], the lower triangle of L (n*n normals, strictly lower
+    part scaled by overlap / sqrt(n), unit diagonal), A (n*n normals), then for
+    each of the k perturbations A_t, H_t, S_t (n*n normals each). Symmetric
+    draws use ``sym_gaussian`` with sigma = 1/sqrt(n)."""
+    if nocc is None:
+        nocc = n // 2
+    rng = np.random.default_rng(seed)
+    q = haar_orthogonal(rng, n)
+    e = np.concatenate([rng.uniform(-1.0, -0.2, nocc), rng.uniform(0.2, 1.0, n - nocc)])
+    lo = np.tril(rng.standard_normal((n, n)), -1) * (overlap / math.sqrt(n))
+    L = lo + np.eye(n)
+    hp = (q * e[None, :]) @ q.T
+    h = L @ hp @ L.T
+    h = 0.5 * (h + h.T)
+    S = L @ L.T
+    S = 0.5 * (S + S.T)
+    sig = 1.0 / math.sqrt(n)
+    a = sym_gaussian(rng, n, sig)
+    at, ht, st = [], [], []
+    for _ in range(k):
+        at.append(sym_gaussian(rng, n, sig))
+        ht.append(sym_gaussian(rng, n, sig))
+        st.append(sym_gaussian(rng, n, sig))
+    return NonOrthProblem(H=h, S=S, A=a, A_t=np.array(at), H_t=np.array(ht), S_t=np.array(st),
+                          e=e, nocc=nocc)
