@@ -150,7 +150,8 @@ typedef struct {
   int ckpt_k;                         /* checkpoint interval the call used (backward chi and
                                          keep_history; SP2_CKPT_AUTO resolved), else 0 */
   int refine_iter;                    /* sp2_scf_response: first iteration (0-based) computed
-                                         in refine_mode, -1 if none */
+                                         in refine_mode, -1 if none; sp2_nonorth_susceptibility:
+                                         Newton-Schulz iterations of S^(-1/2) */
 } sp2_info;
 
 typedef struct sp2_handle_s* sp2_handle_t;
@@ -223,6 +224,28 @@ int sp2_release_history(sp2_handle_t h);
 int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, double kT,
               const void* B, int64_t K, int b_diag_only, int canonical, int n_doublings,
               const sp2_opts* opts, void* D, void* D1, sp2_info* info);
+
+/* Non-orthonormal basis (Sec. V.A): H, S (overlap, symmetric positive definite)
+ * and the observable A in the atomic-orbital representation, N x N (dtype,
+ * device or host). With the Loewdin factor Z = S^(-1/2) (coupled Newton-Schulz
+ * iteration on the device), H^perp = Z H Z, A^perp = Z A Z, D^perp from Eq. DM0,
+ * chi^perp from Eq. DM2, and D = Z D^perp Z. Outputs (N x N, dtype):
+ *   D    the density matrix in the atomic-orbital representation;
+ *   W_H  = Z chi^perp Z;
+ *   W_S  = -sym(S^-1 H W_H) - sym(S^-1 A D), sym(M) = (M + M^T) / 2;
+ *   Z    (nullable) the Loewdin factor.
+ * The derivative of a = Tr[A D] along any basis-set dependent perturbation
+ * (Eq. NonOrthDer with Z_tau = -S^-1 S_tau Z / 2, dual form Tr[A^perp D^perp_tau]
+ * = Tr[chi^perp H^perp_tau]) is then three contractions,
+ *   a_tau = Tr[A_tau D] + Tr[W_H H_tau] + Tr[W_S S_tau],
+ * e.g. with response_contract. opts as for sp2_susceptibility (fixed_m is not
+ * accepted); info is that of the SP2 / susceptibility solve on H^perp with the
+ * product counts of the whole call, and info->refine_iter holds the number of
+ * Newton-Schulz iterations. SP2_EINVAL for an overlap whose Gershgorin bound
+ * is not positive, SP2_ENOCONV if the inverse square root does not converge. */
+int sp2_nonorth_susceptibility(sp2_handle_t h, const void* H, const void* S, int64_t N, int dtype,
+                               double nocc, const void* A, const sp2_opts* opts, void* D,
+                               void* W_H, void* W_S, void* Z, sp2_info* info);
 
 /* Self-consistent first-order response (Appendix, Eq. DM_CP_SCF; its dual is
  * Eq. CP_SCF) with a site-charge interaction: for each of F external site

@@ -133,6 +133,9 @@ EXPORTS = {
     "sp2_fermi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double,
                             C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.POINTER(Opts),
                             C.c_void_p, C.c_void_p, C.POINTER(Info)]),
+    "sp2_nonorth_susceptibility": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                             C.c_double, C.c_void_p, C.POINTER(Opts), C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info)]),
     "response_contract": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "sp2_scf_response": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_int,

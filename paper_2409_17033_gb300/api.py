@@ -26,7 +26,8 @@ import torch
 from . import _lib as L
 
 __all__ = ["Handle", "make_opts", "sp2_density", "sp2_response", "sp2_susceptibility",
-           "sp2_adjoint", "sp2_fermi", "sp2_scf_response", "mlp_forward", "mlp_loss_grad",
+           "sp2_adjoint", "sp2_fermi", "sp2_nonorth_susceptibility", "sp2_scf_response",
+           "mlp_forward", "mlp_loss_grad",
            "mlp_train", "response_contract", "SP2Error"]
 
 SP2Error = L.SP2Error
@@ -196,6 +197,25 @@ def sp2_susceptibility(H, nocc: float, A, direction: str = "forward", diag_only:
                                   C.byref(info))
     h.check(rc, allow_noconv)
     return chi, D, info.to_dict()
+
+
+def sp2_nonorth_susceptibility(H, S, nocc: float, A, mode="fp64", want_z: bool = False,
+                               handle: Handle | None = None, **kw):
+    """Non-orthonormal basis (Sec. V.A): returns (D, W_H, W_S, Z or None, info)
+    so that d Tr[A D] / d tau = Tr[A_t D] + Tr[W_H H_t] + Tr[W_S S_t] for any
+    basis-set dependent perturbation (A_t, H_t, S_t)."""
+    h = handle or default_handle()
+    h.bind_stream()
+    n = H.shape[0]
+    D, WH, WS = (_empty_like(H, (n, n)) for _ in range(3))
+    Z = _empty_like(H, (n, n)) if want_z else None
+    opts, _keep = make_opts(mode, **kw)
+    info = L.Info()
+    rc = h.lib.sp2_nonorth_susceptibility(h.h, _ptr(H), _ptr(S), n, _dtype_code(H), float(nocc),
+                                          _ptr(A), C.byref(opts), _ptr(D), _ptr(WH), _ptr(WS),
+                                          _ptr(Z), C.byref(info))
+    h.check(rc)
+    return D, WH, WS, Z, info.to_dict()
 
 
 def sp2_adjoint(G, handle: Handle):

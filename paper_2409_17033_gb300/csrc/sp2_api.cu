@@ -1293,6 +1293,213 @@ int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, do
   return SP2_OK;
 }
 
+}  // extern "C"
+
+// --------------------------------------------------------------- non-orthonormal basis
+namespace {
+
+// caller matrix (N x N, dtype) -> padded FMat times `scale`, with planes
+int fload(Ctx& c, FMat& f, const void* src, int dtype, double scale) {
+  sp2_handle_t h = c.h;
+  const bool f16 = c.mode == SP2_MODE_FP16X2;
+  if (f16) CK(cudaMemsetAsync(f.amax, 0, sizeof(float), h->stream));
+  CK(launch_init(src, c.n, c.np, 1, dtype, 0, 1, 0.0, scale, c.mode, f.m, nullptr, 0,
+                 f16 ? f.amax : nullptr, h->stream));
+  c.kernels++;
+  if (f16) TRY(fplanes(c, f));
+  return SP2_OK;
+}
+
+// C = sym(L M R) for symmetric R: the middle product's planes are formed for its
+// use as the row operand of the second product (scratch T1, T2)
+int fsandwich(Ctx& c, FMat& C, const FMat& L, const FMat& Mid, const FMat& R, FMat& T1, FMat& T2) {
+  TRY(fprod(c, T1, L, Mid));
+  TRY(fplanes(c, T1));
+  TRY(fprod(c, T2, T1, R));
+  return fcomb(c, C, &T2, 0.5, nullptr, 0.0, nullptr, 0.0, 0.0, true);
+}
+
+// ||T - I||_F^2 of the padded master (zero outside the caller's block), FP64
+int dist_to_identity(Ctx& c, const FMat& T, double* out) {
+  sp2_handle_t h = c.h;
+  void* p;
+  TRY(ws(h, "no.red", 4 * sizeof(double), &p));
+  double* d = static_cast<double*>(p);
+  const int mdt = c.mode == SP2_MODE_FP64 ? SP2_F64 : SP2_F32;
+  const int np_ = contract_nparts(c.np, 0);
+  void* part;
+  TRY(ws(h, "no.part", (size_t)np_ * sizeof(double), &part));
+  CK(launch_contract(T.m.master, 1, T.m.master, 1, c.np, mdt, 0, static_cast<double*>(part), np_,
+                     d, h->stream));
+  CK(launch_trace(c.mode, T.m.master, c.np, c.n, d + 1, h->stream));
+  double hv[2];
+  CK(cudaMemcpyAsync(hv, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  c.kernels += 2;
+  *out = hv[0] - 2.0 * hv[1] + (double)c.n;
+  return SP2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sp2_nonorth_susceptibility(sp2_handle_t h, const void* H, const void* S, int64_t N, int dtype,
+                               double nocc, const void* A, const sp2_opts* opts_in, void* D,
+                               void* WH, void* WS, void* Zout, sp2_info* info) {
+  TRY(check_common(h, H, N, dtype, nocc));
+  if (N > 0 && (!S || !A || !D || !WH || !WS)) return fail(h, SP2_EINVAL, "null pointer");
+  sp2_opts o = resolve(opts_in);
+  TRY(validate_opts(h, &o));
+  if (o.fixed_m > 0) return fail(h, SP2_EINVAL, "fixed_m is not supported here");
+  if (info) memset(info, 0, sizeof *info);
+  if (N == 0) {
+    if (info) info->converged = 1;
+    return SP2_OK;
+  }
+  const int mode = o.mode;
+  const int64_t np = pad_n(N);
+  const size_t mb = (size_t)N * N * dsize(dtype);
+  const void *Hd, *Sd, *Ad;
+  TRY(stage_in(h, "H", H, mb, &Hd));
+  TRY(stage_in(h, "no.S", S, mb, &Sd));
+  TRY(stage_in(h, "B", A, mb, &Ad));
+  OutStage od, oh, os, oz;
+  TRY(stage_out(h, "no.D", D, mb, &od));
+  TRY(stage_out(h, "no.WH", WH, mb, &oh));
+  TRY(stage_out(h, "no.WS", WS, mb, &os));
+  if (Zout) TRY(stage_out(h, "no.Z", Zout, mb, &oz));
+  Ctx c;
+  TRY(make_ctx(h, mode, N, np, o.time_kernels != 0, &c));
+  CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));
+
+  // Loewdin factor Z = S^(-1/2) by the coupled Newton-Schulz iteration on S / s0,
+  // s0 the Gershgorin upper bound of S (spectrum of S / s0 in (0, 1]):
+  //   T = (3 I - Zk Yk) / 2,  Yk <- Yk T -> (S/s0)^(1/2),  Zk <- T Zk -> (S/s0)^(-1/2).
+  // Every iterate is a polynomial in S, so all factors commute and are symmetric.
+  const int nb = bounds_nparts(N);
+  void* bp;
+  TRY(ws(h, "bounds.part", nb * sizeof(double2), &bp));
+  CK(launch_bounds(Sd, N, dtype, static_cast<double2*>(bp), nb, h->d_state, h->stream));
+  c.kernels += 2;
+  TRY(poll_state(h));
+  const double s0 = h->h_state->bounds[1];
+  if (!std::isfinite(s0) || !(s0 > 0.0))
+    return fail(h, SP2_EINVAL, "overlap matrix with non-positive or non-finite Gershgorin bound");
+  FMat Y, Zk, T, P, Q, Q2, Z, Sinv, Hm, Am, Hp, Ap, Dp, Cp, Dm, Wh, Ws;
+  TRY(fmat(h, "no.Y", np, mode, &Y));
+  TRY(fmat(h, "no.Zk", np, mode, &Zk));
+  TRY(fmat(h, "no.T", np, mode, &T));
+  TRY(fmat(h, "no.P", np, mode, &P));
+  TRY(fmat(h, "no.Q", np, mode, &Q));
+  TRY(fmat(h, "no.Q2", np, mode, &Q2));
+  TRY(fload(c, Y, Sd, dtype, 1.0 / s0));
+  TRY(fcomb(c, Zk, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, true));
+  const double tol = mode == SP2_MODE_FP64 ? 1e-26 * (double)N : 1e-12 * (double)N;
+  double prev = 0.0;
+  int its = 0, stall = 0;
+  for (; its < 100; ++its) {
+    TRY(fprod(c, P, Zk, Y));
+    TRY(fcomb(c, T, &P, -0.25, nullptr, 0.0, nullptr, 0.0, 1.5, true));
+    double e;
+    TRY(dist_to_identity(c, T, &e));  // ||T - I||^2 = ||I - Zk Yk||^2 / 4
+    if (!std::isfinite(e)) return fail(h, SP2_ENONFINITE, "non-finite Newton-Schulz residual");
+    if (e <= tol) break;
+    // below 1e-6 an iteration that does not halve the residual has reached the
+    // rounding floor of the mode (twice in a row ends the iteration)
+    if (its > 0 && e < 1e-6 * (double)N && e > 0.25 * prev) {
+      if (++stall >= 2) break;
+    } else {
+      stall = 0;
+    }
+    prev = e;
+    TRY(fprod(c, Q, Y, T));
+    TRY(fprod(c, Q2, T, Zk));
+    TRY(fcomb(c, Y, &Q, 0.5, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+    TRY(fcomb(c, Zk, &Q2, 0.5, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+  }
+  if (its >= 100) return fail(h, SP2_ENOCONV, "inverse square root of S did not converge");
+  TRY(fmat(h, "no.Z", np, mode, &Z));
+  TRY(fmat(h, "no.Sinv", np, mode, &Sinv));
+  TRY(fcomb(c, Z, &Zk, 0.5 / std::sqrt(s0), nullptr, 0.0, nullptr, 0.0, 0.0, true));
+  TRY(fprod(c, Q, Z, Z));
+  TRY(fcomb(c, Sinv, &Q, 0.5, nullptr, 0.0, nullptr, 0.0, 0.0, true));  // S^(-1) = Z Z
+
+  // orthonormalised H and A (Sec. V.A congruences)
+  TRY(fmat(h, "no.H", np, mode, &Hm));
+  TRY(fmat(h, "no.A", np, mode, &Am));
+  TRY(fmat(h, "no.Hp", np, mode, &Hp));
+  TRY(fmat(h, "no.Ap", np, mode, &Ap));
+  TRY(fload(c, Hm, Hd, dtype, 1.0));
+  TRY(fload(c, Am, Ad, dtype, 1.0));
+  TRY(fsandwich(c, Hp, Z, Hm, Z, P, Q));
+  TRY(fsandwich(c, Ap, Z, Am, Z, P, Q));
+
+  // D^perp and chi^(A^perp): the SP2 density and the backward susceptibility (Eq. DM2)
+  const int idt = mode == SP2_MODE_FP64 ? SP2_F64 : SP2_F32;
+  const size_t ib = (size_t)N * N * dsize(idt);
+  void *hpn, *apn, *dpn, *cpn;
+  TRY(ws(h, "no.Hpn", ib, &hpn));
+  TRY(ws(h, "no.Apn", ib, &apn));
+  TRY(ws(h, "no.Dpn", ib, &dpn));
+  TRY(ws(h, "no.Cpn", ib, &cpn));
+  CK(launch_copy_out(Hp.m, N, np, 1, mode, 1.0, hpn, idt, h->stream));
+  CK(launch_copy_out(Ap.m, N, np, 1, mode, 1.0, apn, idt, h->stream));
+  c.kernels += 2;
+  const int64_t k0 = c.kernels, l0 = c.launches;
+  const double f0 = c.flops, a0 = c.alg;
+  sp2_info si;
+  TRY(sp2_susceptibility(h, hpn, N, idt, nocc, apn, 1, 0, 1, &o, dpn, cpn, &si));
+  TRY(make_ctx(h, mode, N, np, o.time_kernels != 0, &c));  // fresh partials after the solve
+  c.kernels = k0 + si.kernel_launches;
+  c.launches = l0 + si.n_gemm_launches;
+  c.flops = f0 + si.executed_flops;
+  c.alg = a0 + si.algorithmic_flops;
+  c.st = h->d_state;
+  CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));
+
+  // back to the atomic-orbital representation and the dual weights:
+  //   D = Z D^perp Z,  W_H = Z chi^perp Z,  W_S = -sym(S^-1 H W_H) - sym(S^-1 A D)
+  TRY(fmat(h, "no.Dp", np, mode, &Dp));
+  TRY(fmat(h, "no.Cp", np, mode, &Cp));
+  TRY(fmat(h, "no.Dm", np, mode, &Dm));
+  TRY(fmat(h, "no.Wh", np, mode, &Wh));
+  TRY(fmat(h, "no.Ws", np, mode, &Ws));
+  TRY(fload(c, Dp, dpn, idt, 1.0));
+  TRY(fload(c, Cp, cpn, idt, 1.0));
+  TRY(fsandwich(c, Dm, Z, Dp, Z, P, Q));
+  TRY(fsandwich(c, Wh, Z, Cp, Z, P, Q));
+  TRY(fprod(c, P, Sinv, Hm));
+  TRY(fplanes(c, P));
+  TRY(fprod(c, Q, P, Wh));           // M = S^-1 H W_H
+  TRY(fprod(c, P, Sinv, Am));
+  TRY(fplanes(c, P));
+  TRY(fprod(c, Q2, P, Dm));          // S^-1 A D
+  TRY(fcomb(c, Ws, &Q, -0.5, &Q2, -0.5, nullptr, 0.0, 0.0, false));
+  CK(launch_copy_out(Dm.m, N, np, 1, mode, 1.0, od.dev, dtype, h->stream));
+  CK(launch_copy_out(Wh.m, N, np, 1, mode, 1.0, oh.dev, dtype, h->stream));
+  CK(launch_copy_out(Ws.m, N, np, 1, mode, 1.0, os.dev, dtype, h->stream));
+  c.kernels += 3;
+  if (Zout) {
+    CK(launch_copy_out(Z.m, N, np, 1, mode, 1.0, oz.dev, dtype, h->stream));
+    c.kernels++;
+    TRY(finish_out(h, oz));
+  }
+  TRY(finish_out(h, od));
+  TRY(finish_out(h, oh));
+  TRY(finish_out(h, os));
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) {
+    *info = si;
+    info->n_gemm_launches = c.launches;
+    info->executed_flops = c.flops;
+    info->algorithmic_flops = c.alg;
+    info->kernel_launches = c.kernels;
+    info->refine_iter = its;   // Newton-Schulz iterations of the inverse square root
+  }
+  return SP2_OK;
+}
+
 int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, int64_t K, int64_t N,
                       int dtype, int q_diag_only, double* out) {
   if (!h) return SP2_EINVAL;
