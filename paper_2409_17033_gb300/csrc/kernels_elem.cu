@@ -434,6 +434,67 @@ __global__ void k_contract_dense(const T* __restrict__ P, const T* __restrict__ 
   if (threadIdx.x == 0) part[pair * nparts + blockIdx.x] = acc;
 }
 
+// FP32 inputs: exact products and sums at FP32 cost. TwoProduct splits a*b into
+// p + e exactly (e = fma(a, b, -p)); TwoSum adds p to the running pair (s, c)
+// without loss; the small terms e and c are summed in FP32, their rounding far
+// below 2^-40 of the magnitudes involved. Each thread converts once to FP64 at
+// the end. A block covers one slice of the N^2 entries for up to kCtrKT
+// perturbations Q_k, so the shared left factor P_l is read once per kCtrKT.
+constexpr int kCtrKT = 8;
+
+// (the _rn intrinsics are never contracted into FMAs, which would break both
+// error-free transformations)
+__device__ __forceinline__ void acc_exact(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  c = __fadd_rn(c, __fadd_rn(err, e));
+  s = t;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) k_contract_dense_f32(const float* __restrict__ P,
+                                                           const float* __restrict__ Q, int64_t K,
+                                                           int64_t nn, double* part, int nparts) {
+  const int64_t ktiles = (K + kCtrKT - 1) / kCtrKT;
+  const int64_t l = blockIdx.y / ktiles, k0 = (blockIdx.y % ktiles) * kCtrKT;
+  const int kn = (int)((K - k0) < kCtrKT ? (K - k0) : kCtrKT);
+  const float* p = P + l * nn;
+  float s[kCtrKT], c[kCtrKT];
+#pragma unroll
+  for (int kk = 0; kk < kCtrKT; ++kk) s[kk] = c[kk] = 0.0f;
+  const int64_t nv = nn / VEC;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (VEC == 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p) + t);
+#pragma unroll
+      for (int kk = 0; kk < kCtrKT; ++kk) {
+        if (kk < kn) {
+          const float4 b = __ldcs(reinterpret_cast<const float4*>(Q + (k0 + kk) * nn) + t);
+          acc_exact(s[kk], c[kk], a.x, b.x);
+          acc_exact(s[kk], c[kk], a.y, b.y);
+          acc_exact(s[kk], c[kk], a.z, b.z);
+          acc_exact(s[kk], c[kk], a.w, b.w);
+        }
+      }
+    } else {
+      const float a = p[t];
+#pragma unroll
+      for (int kk = 0; kk < kCtrKT; ++kk)
+        if (kk < kn) acc_exact(s[kk], c[kk], a, Q[(k0 + kk) * nn + t]);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < kCtrKT; ++kk) {
+    if (kk >= kn) break;   // uniform across the block
+    const double v = block_sum((double)s[kk] + (double)c[kk]);
+    if (threadIdx.x == 0) part[(l * K + k0 + kk) * nparts + blockIdx.x] = v;
+  }
+}
+
 template <typename T>
 __global__ void k_contract_diag(const T* __restrict__ P, const T* __restrict__ Q, int64_t K,
                                 int64_t n, double* part, int nparts) {
@@ -532,11 +593,13 @@ cudaError_t launch_split_scaled(MatBuf m, int64_t np, ScaleBuf sc, int slot, cud
   return cudaGetLastError();
 }
 
+// blocks per (l, k) pair: one per 4096 entries, at most 1216 (8 blocks of 256
+// threads per SM on 152 SMs, enough loads in flight for HBM with one pair)
 int contract_nparts(int64_t n, int q_diag) {
   int64_t work = q_diag ? n : n * n;
   int64_t g = (work + 256 * 16 - 1) / (256 * 16);
   if (g < 1) g = 1;
-  if (g > 304) g = 304;
+  if (g > 1216) g = 1216;
   return (int)g;
 }
 
@@ -556,10 +619,22 @@ cudaError_t launch_contract(const void* P, int64_t L, const void* Q, int64_t K, 
     if (q_diag)
       k_contract_diag<float><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
                                                   static_cast<const float*>(Q), K, n, part, nparts);
-    else
-      k_contract_dense<float><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
-                                                   static_cast<const float*>(Q), K, n * n, part,
+    else {
+      // float4 path when every matrix starts on a 16-byte boundary
+      const int64_t nn = n * n;
+      const bool v4 = nn % 4 == 0 && ((reinterpret_cast<uintptr_t>(P) |
+                                       reinterpret_cast<uintptr_t>(Q)) & 15u) == 0;
+      const int64_t ktiles = (K + kCtrKT - 1) / kCtrKT;
+      dim3 g2((unsigned)nparts, (unsigned)(L * ktiles));
+      if (v4)
+        k_contract_dense_f32<4><<<g2, 256, 0, s>>>(static_cast<const float*>(P),
+                                                   static_cast<const float*>(Q), K, nn, part,
                                                    nparts);
+      else
+        k_contract_dense_f32<1><<<g2, 256, 0, s>>>(static_cast<const float*>(P),
+                                                   static_cast<const float*>(Q), K, nn, part,
+                                                   nparts);
+    }
   }
   k_contract_final<<<(unsigned)(L * K), 256, 0, s>>>(part, nparts, out);
   return cudaGetLastError();

@@ -1521,7 +1521,12 @@ int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, i
   TRY(stage_in(h, "Q", Q, (size_t)K * (q_diag_only ? N : N * N) * dsize(dtype), &Qd));
   OutStage oo;
   TRY(stage_out(h, "out", out, (size_t)L * K * sizeof(double), &oo));
-  const int np_ = contract_nparts(N, q_diag_only);
+  int np_ = contract_nparts(N, q_diag_only);
+  if (L * K >= 8 && np_ > 304) np_ = 304;   // many pairs already fill the GPU
+  if ((int64_t)np_ * L * K > (int64_t)1 << 24) {   // partials of many pairs: at most 128 MiB
+    const int64_t m = ((int64_t)1 << 24) / (L * K);
+    np_ = (int)(m < 1 ? 1 : m);
+  }
   void* part;
   TRY(ws(h, "contract.part", (size_t)L * K * np_ * sizeof(double), &part));
   CK(launch_contract(Pd, L, Qd, K, N, dtype, q_diag_only, static_cast<double*>(part), np_,
