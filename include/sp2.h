@@ -286,6 +286,11 @@ typedef struct {
                            and M again, and Anderson restarts its history. 0 = never
                            switch. Lets split-precision responses do the bulk of the
                            iterations and FP32 / FP64 ones go below their rounding floor. */
+  double kT;            /* > 0: finite-temperature responses (Sec. V.B recursion, as in
+                           sp2_fermi) at chemical potential mu; 0: zero temperature (Eq. DM1) */
+  double mu;
+  int n_doublings;      /* finite T: doublings of the recursion (0 = 20) */
+  int canonical;        /* finite T: 1 = canonical responses (mu_1 with Tr[D1] = 0) */
 } sp2_scf_opts;
 
 int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc, int norb,

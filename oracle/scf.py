@@ -47,6 +47,22 @@ def chi0_sites(e: np.ndarray, V: np.ndarray, nocc: int, norb: int) -> np.ndarray
     return out
 
 
+def chi0_sites_fermi(e: np.ndarray, V: np.ndarray, mu: float, kT: float, norb: int,
+                     canonical: bool = True) -> np.ndarray:
+    """Finite-temperature chi0_ab = d q_a / d u_b (Sec. V.B): the Daleckii-Krein
+    response of the Fermi function to each site-diagonal perturbation, with
+    the canonical mu_1 (Tr[D1] = 0) when asked, then summed over site a."""
+    n = V.shape[0]
+    ns = n // norb
+    out = np.zeros((ns, ns))
+    for b in range(ns):
+        P = np.zeros(n)
+        P[b * norb:(b + 1) * norb] = 1.0
+        D1 = exact.response_fermi(e, V, mu, kT, np.diag(P), canonical=canonical)
+        out[:, b] = np.diag(D1).reshape(ns, norb).sum(axis=1)
+    return out
+
+
 def scf_exact(chi0: np.ndarray, K: np.ndarray, Vext: np.ndarray) -> np.ndarray:
     """q* = (I - chi0 K)^(-1) chi0 V_ext for every field (rows of Vext)."""
     ns = chi0.shape[0]

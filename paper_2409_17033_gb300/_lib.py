@@ -107,6 +107,10 @@ class ScfOpts(C.Structure):
         ("bf16_infer", C.c_int),
         ("refine_mode", C.c_int),
         ("refine_below", C.c_double),
+        ("kT", C.c_double),
+        ("mu", C.c_double),
+        ("n_doublings", C.c_int),
+        ("canonical", C.c_int),
     ]
 
 

@@ -256,6 +256,8 @@ def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
                      alpha: float = 0.3, history: int = 8, tol: float = 1e-6, max_iter: int = 100,
                      W1=None, W2=None, bf16_infer: bool = True, record: bool = False,
                      mode="fp64", refine_mode=None, refine_below: float = 0.0,
+                     kT: float = 0.0, mu: float = 0.0, n_doublings: int = 20,
+                     canonical: bool = True,
                      handle: Handle | None = None, allow_noconv: bool = False,
                      return_info: bool = False, **kw):
     """Self-consistent site-charge response for F fields (rows of Vext, float64).
@@ -263,7 +265,9 @@ def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
     traj_q) or None), plus the info dict when return_info; q and the
     trajectories live where Vext lives. refine_mode / refine_below: compute the
     responses in another arithmetic mode once the residual is below
-    refine_below or stalls (info["refine_iter"] = first such iteration)."""
+    refine_below or stalls (info["refine_iter"] = first such iteration).
+    kT > 0: finite-temperature responses at chemical potential mu (Sec. V.B;
+    canonical mu_1 by default)."""
     h = handle or default_handle()
     h.bind_stream()
     n = H.shape[0]
@@ -278,6 +282,10 @@ def sp2_scf_response(H, nocc: float, norb: int, K, Vext, mixer: str = "linear",
     so.W2 = _ptr(W2) if W2 is not None else None
     so.hidden = int(W1.shape[0]) if W1 is not None else 0
     so.bf16_infer = 1 if bf16_infer else 0
+    so.kT = float(kT)
+    so.mu = float(mu)
+    so.n_doublings = int(n_doublings)
+    so.canonical = 1 if canonical else 0
     if refine_mode is not None:
         so.refine_mode = L.MODES[refine_mode] if isinstance(refine_mode, str) else int(refine_mode)
         so.refine_below = float(refine_below)

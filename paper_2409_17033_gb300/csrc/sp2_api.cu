@@ -1097,6 +1097,186 @@ int sp2_release_history(sp2_handle_t h) {
 }
 
 
+}  // extern "C"
+
+// --------------------------------------------------------------- finite temperature driver
+namespace {
+
+// The forward pass of the finite-temperature recursion (Sec. V.B, tanh doubling
+// delta_{j+1} = 2 delta_j W_j, W_j = (I + 4 delta_j^2)^-1) with its history, kept
+// for any number of responses; with `canonical`, also the response R_I to the
+// identity and its trace, for mu_1 such that Tr[D1] = 0.
+struct FermiState {
+  int n = 0;                 // doublings
+  double cst = 0.0;          // beta / 2^(n+2)
+  double emin = 0.0, emax = 0.0;
+  bool canonical = false;
+  std::vector<FMat> dl, W;   // delta_0..delta_n, W_0..W_{n-1}
+  FMat P, S, T, U, Z2[2];    // scratch of the forward pass and the responses
+  FMat dd[2], E, F1, dW, G1, RI;
+  double trI = 0.0;
+  void* tr = nullptr;        // 2 device doubles
+};
+
+int fermi_response(Ctx& c, FermiState& fs, const void* src, int dtype, int diag, bool isI,
+                   FMat** result);
+
+int fermi_setup(Ctx& c, FermiState& fs, const void* Hd, int64_t N, int dtype, double mu, double kT,
+                int n_doublings, bool canonical, bool responses) {
+  sp2_handle_t h = c.h;
+  const int mode = c.mode;
+  const int64_t np = c.np;
+  CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));  // never halted
+  // spectral bound of H - mu I (Gershgorin, Sec. II estimates)
+  const int nb = bounds_nparts(N);
+  void* bp;
+  TRY(ws(h, "bounds.part", nb * sizeof(double2), &bp));
+  CK(launch_bounds(Hd, N, dtype, static_cast<double2*>(bp), nb, h->d_state, h->stream));
+  c.kernels += 2;
+  TRY(poll_state(h));
+  fs.emin = h->h_state->bounds[0];
+  fs.emax = h->h_state->bounds[1];
+  if (!std::isfinite(fs.emin) || !std::isfinite(fs.emax))
+    return fail(h, SP2_ENONFINITE, "non-finite spectral bounds (NaN/Inf in H)");
+  fs.cst = 1.0 / (kT * std::ldexp(1.0, n_doublings + 2));
+  double b = fs.cst * std::fmax(std::fabs(fs.emax - mu), std::fabs(fs.emin - mu));
+  if (!(b < 0.5))
+    return fail(h, SP2_EINVAL, "n_doublings = %d too small: |e - mu| / (kT 2^(n+2)) reaches %g >= 1/2",
+                n_doublings, b);
+  const double tol = mode == SP2_MODE_FP64 ? 1e-17 : 1e-8;
+  const int n = n_doublings;
+  fs.n = n;
+  fs.canonical = canonical;
+  fs.dl.assign(n + 1, FMat{});
+  fs.W.assign(n, FMat{});
+  for (int j = 0; j <= n; ++j) TRY(fmat(h, "ft.d" + std::to_string(j), np, mode, &fs.dl[j]));
+  for (int j = 0; j < n; ++j) TRY(fmat(h, "ft.W" + std::to_string(j), np, mode, &fs.W[j]));
+  TRY(fmat(h, "ft.P", np, mode, &fs.P));
+  TRY(fmat(h, "ft.S", np, mode, &fs.S));
+  TRY(fmat(h, "ft.T", np, mode, &fs.T));
+  TRY(fmat(h, "ft.U", np, mode, &fs.U));
+  TRY(fmat(h, "ft.Z0", np, mode, &fs.Z2[0]));
+  TRY(fmat(h, "ft.Z1", np, mode, &fs.Z2[1]));
+  // delta_0 = c mu I - c H (planes with scale 1: |delta| < 1/2)
+  CK(launch_init(Hd, N, np, 1, dtype, 0, 0, fs.cst * mu, -fs.cst, mode, fs.dl[0].m, nullptr, 0,
+                 nullptr, h->stream));
+  c.kernels++;
+  if (mode == SP2_MODE_FP16X2) {
+    const float one = 1.0f;
+    CK(cudaMemcpyAsync(fs.dl[0].scale, &one, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  for (int j = 0; j < n; ++j) {
+    // S = I + 4 delta^2, symmetrised: I + 2 (P + P^T)
+    TRY(fprod(c, fs.P, fs.dl[j], fs.dl[j]));
+    TRY(fcomb(c, fs.S, &fs.P, 2.0, nullptr, 0.0, nullptr, 0.0, 1.0, true));
+    // W = S^{-1} by Newton-Schulz: Z <- 2 Z - sym(Z (S Z))
+    const int kns = ns_iterations(b, tol);
+    const double z0 = 2.0 / (2.0 + 4.0 * b * b);
+    int zi = 0;
+    FMat* Zc = (kns == 0) ? &fs.W[j] : &fs.Z2[0];
+    TRY(fcomb(c, *Zc, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, z0, true));
+    for (int it = 0; it < kns; ++it) {
+      FMat& Zin = *Zc;
+      FMat& Zout = (it == kns - 1) ? fs.W[j] : fs.Z2[1 - zi];
+      TRY(fprod(c, fs.T, fs.S, Zin));
+      TRY(fplanes(c, fs.T));
+      TRY(fprod(c, fs.U, Zin, fs.T));
+      TRY(fcomb(c, Zout, &fs.U, -0.5, nullptr, 0.0, &Zin, 2.0, 0.0, true));
+      zi = 1 - zi;
+      Zc = &Zout;
+    }
+    // delta_{j+1} = 2 delta W, symmetrised: V + V^T with V = delta W
+    TRY(fprod(c, fs.P, fs.dl[j], fs.W[j]));
+    TRY(fcomb(c, fs.dl[j + 1], &fs.P, 1.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+    b = 2.0 * b / (1.0 + 4.0 * b * b);
+  }
+  if (!responses) return SP2_OK;
+  TRY(fmat(h, "ft.dd0", np, mode, &fs.dd[0]));
+  TRY(fmat(h, "ft.dd1", np, mode, &fs.dd[1]));
+  TRY(fmat(h, "ft.E", np, mode, &fs.E));
+  TRY(fmat(h, "ft.F1", np, mode, &fs.F1));
+  TRY(fmat(h, "ft.dW", np, mode, &fs.dW));
+  TRY(fmat(h, "ft.G1", np, mode, &fs.G1));
+  TRY(ws(h, "ft.tr", 2 * sizeof(double), &fs.tr));
+  if (canonical) {
+    TRY(fmat(h, "ft.RI", np, mode, &fs.RI));
+    void* ones = nullptr;
+    TRY(ws(h, "ft.ones", (size_t)N * dsize(dtype), &ones));
+    std::vector<double> h1(N, 1.0);
+    std::vector<float> h1f(N, 1.0f);
+    CK(cudaMemcpyAsync(ones, dtype == SP2_F64 ? (const void*)h1.data() : (const void*)h1f.data(),
+                       (size_t)N * dsize(dtype), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    FMat* r;
+    TRY(fermi_response(c, fs, ones, dtype, 1, true, &r));   // the response to I first
+  }
+  return SP2_OK;
+}
+
+// First-order response of f(H) to B (chain rule of every doubling); canonical
+// adds -(Tr D1 / Tr R_I) R_I. *result points at the FMat holding it (scratch
+// of fs, valid until the next response).
+int fermi_response(Ctx& c, FermiState& fs, const void* src, int dtype, int diag, bool isI,
+                   FMat** result) {
+  sp2_handle_t h = c.h;
+  const int mode = c.mode;
+  const int n = fs.n;
+  double* tr = static_cast<double*>(fs.tr);
+  int cur = 0;
+  FMat& d0 = fs.dd[0];
+  if (mode == SP2_MODE_FP16X2) CK(cudaMemsetAsync(d0.amax, 0, sizeof(float), h->stream));
+  CK(launch_init(src, c.n, c.np, 1, dtype, diag, 0, 0.0, -fs.cst, mode, d0.m, nullptr, 0,
+                 mode == SP2_MODE_FP16X2 ? d0.amax : nullptr, h->stream));
+  c.kernels++;
+  if (mode == SP2_MODE_FP16X2) TRY(fplanes(c, d0));
+  for (int j = 0; j < n; ++j) {
+    FMat& din = fs.dd[cur];
+    FMat& dout = (j == n - 1 && isI) ? fs.RI : fs.dd[1 - cur];
+    // E = d delta delta + delta d delta = Z1 + Z1^T, Z1 = d delta * delta
+    TRY(fprod(c, fs.P, din, fs.dl[j]));
+    TRY(fcomb(c, fs.E, &fs.P, 1.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+    // dW = -4 W E W = -2 (F2 + F2^T), F2 = (W E) W
+    TRY(fprod(c, fs.F1, fs.W[j], fs.E));
+    TRY(fplanes(c, fs.F1));
+    TRY(fprod(c, fs.U, fs.F1, fs.W[j]));
+    TRY(fcomb(c, fs.dW, &fs.U, -2.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
+    // d delta' = 2 (d delta W + delta dW) = (G1 + G1^T) + (G2 + G2^T)
+    TRY(fprod(c, fs.G1, din, fs.W[j]));
+    TRY(fprod(c, fs.T, fs.dl[j], fs.dW));
+    TRY(fcomb(c, dout, &fs.G1, 1.0, &fs.T, 1.0, nullptr, 0.0, 0.0, j < n - 1));
+    cur = 1 - cur;
+  }
+  if (isI) {
+    CK(launch_trace(mode, fs.RI.m.master, c.np, c.n, tr + 1, h->stream));
+    CK(cudaMemcpyAsync(&h->h_state->bounds[1], tr + 1, sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    fs.trI = h->h_state->bounds[1];
+    c.kernels++;
+    *result = &fs.RI;
+    return SP2_OK;
+  }
+  FMat& res = fs.dd[cur];
+  *result = &res;
+  if (fs.canonical) {
+    CK(launch_trace(mode, res.m.master, c.np, c.n, tr, h->stream));
+    CK(cudaMemcpyAsync(&h->h_state->bounds[0], tr, sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double trk = h->h_state->bounds[0];
+    c.kernels++;
+    // res - (trk / trI) RI, written as (a/2)(RI + RI^T) + res (RI is exactly symmetric)
+    TRY(fcomb(c, fs.G1, &fs.RI, -0.5 * trk / fs.trI, nullptr, 0.0, &res, 1.0, 0.0, false));
+    *result = &fs.G1;
+  }
+  return SP2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, double kT,
               const void* B, int64_t K, int b_diag_only, int canonical, int n_doublings,
               const sp2_opts* opts_in, void* D, void* D1, sp2_info* info) {
@@ -1124,170 +1304,34 @@ int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, do
   if (K > 0) TRY(stage_out(h, "Y", D1, (size_t)K * mb, &oy));
   Ctx c;
   TRY(make_ctx(h, mode, N, np, o.time_kernels != 0, &c));
-  CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));  // never halted
-
-  // spectral bound of H - mu I (Gershgorin, Sec. II estimates)
-  const int nb = bounds_nparts(N);
-  void* bp;
-  TRY(ws(h, "bounds.part", nb * sizeof(double2), &bp));
-  CK(launch_bounds(Hd, N, dtype, static_cast<double2*>(bp), nb, h->d_state, h->stream));
-  c.kernels += 2;
-  TRY(poll_state(h));
-  const double emin = h->h_state->bounds[0], emax = h->h_state->bounds[1];
-  if (!std::isfinite(emin) || !std::isfinite(emax))
-    return fail(h, SP2_ENONFINITE, "non-finite spectral bounds (NaN/Inf in H)");
-  const double cst = 1.0 / (kT * std::ldexp(1.0, n_doublings + 2));
-  double b = cst * std::fmax(std::fabs(emax - mu), std::fabs(emin - mu));
-  if (!(b < 0.5))
-    return fail(h, SP2_EINVAL, "n_doublings = %d too small: |e - mu| / (kT 2^(n+2)) reaches %g >= 1/2",
-                n_doublings, b);
-  const double tol = mode == SP2_MODE_FP64 ? 1e-17 : 1e-8;
-  const int n = n_doublings;
-
-  // forward pass: store delta_j and W_j, j = 0..n-1
-  std::vector<FMat> dl(n + 1), W(n);
-  for (int j = 0; j <= n; ++j) TRY(fmat(h, "ft.d" + std::to_string(j), np, mode, &dl[j]));
-  for (int j = 0; j < n; ++j) TRY(fmat(h, "ft.W" + std::to_string(j), np, mode, &W[j]));
-  FMat P, S, T, U, Z2[2];
-  TRY(fmat(h, "ft.P", np, mode, &P));
-  TRY(fmat(h, "ft.S", np, mode, &S));
-  TRY(fmat(h, "ft.T", np, mode, &T));
-  TRY(fmat(h, "ft.U", np, mode, &U));
-  TRY(fmat(h, "ft.Z0", np, mode, &Z2[0]));
-  TRY(fmat(h, "ft.Z1", np, mode, &Z2[1]));
-  // delta_0 = c mu I - c H (planes with scale 1: |delta| < 1/2)
-  CK(launch_init(Hd, N, np, 1, dtype, 0, 0, cst * mu, -cst, mode, dl[0].m, nullptr, 0, nullptr,
-                 h->stream));
-  c.kernels++;
-  if (mode == SP2_MODE_FP16X2) {
-    const float one = 1.0f;
-    CK(cudaMemcpyAsync(dl[0].scale, &one, sizeof(float), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-  }
-  for (int j = 0; j < n; ++j) {
-    // S = I + 4 delta^2, symmetrised: I + 2 (P + P^T)
-    TRY(fprod(c, P, dl[j], dl[j]));
-    TRY(fcomb(c, S, &P, 2.0, nullptr, 0.0, nullptr, 0.0, 1.0, true));
-    // W = S^{-1} by Newton-Schulz: Z <- 2 Z - sym(Z (S Z))
-    const int kns = ns_iterations(b, tol);
-    const double z0 = 2.0 / (2.0 + 4.0 * b * b);
-    int zi = 0;
-    FMat* Zc = (kns == 0) ? &W[j] : &Z2[0];
-    TRY(fcomb(c, *Zc, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, z0, true));
-    for (int it = 0; it < kns; ++it) {
-      FMat& Zin = *Zc;
-      FMat& Zout = (it == kns - 1) ? W[j] : Z2[1 - zi];
-      TRY(fprod(c, T, S, Zin));
-      TRY(fplanes(c, T));
-      TRY(fprod(c, U, Zin, T));
-      TRY(fcomb(c, Zout, &U, -0.5, nullptr, 0.0, &Zin, 2.0, 0.0, true));
-      zi = 1 - zi;
-      Zc = &Zout;
-    }
-    // delta_{j+1} = 2 delta W, symmetrised: V + V^T with V = delta W
-    TRY(fprod(c, P, dl[j], W[j]));
-    TRY(fcomb(c, dl[j + 1], &P, 1.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
-    b = 2.0 * b / (1.0 + 4.0 * b * b);
-  }
+  FermiState fs;
+  TRY(fermi_setup(c, fs, Hd, N, dtype, mu, kT, n_doublings, canonical != 0, K > 0));
   // D = I/2 + delta_n
   if (D) {
-    TRY(fcomb(c, P, nullptr, 0.0, nullptr, 0.0, &dl[n], 1.0, 0.5, false));
-    CK(launch_copy_out(P.m, N, np, 1, mode, 1.0, od.dev, dtype, h->stream));
+    TRY(fcomb(c, fs.P, nullptr, 0.0, nullptr, 0.0, &fs.dl[fs.n], 1.0, 0.5, false));
+    CK(launch_copy_out(fs.P.m, N, np, 1, mode, 1.0, od.dev, dtype, h->stream));
     c.kernels++;
     TRY(finish_out(h, od));
   }
-
-  // responses (each perturbation through the stored history); canonical adds
-  // the response to I, and D1_k -= (Tr D1_k / Tr R_I) R_I
-  if (K > 0) {
-    FMat dd[2], E, F1, dW, G1, RI;
-    TRY(fmat(h, "ft.dd0", np, mode, &dd[0]));
-    TRY(fmat(h, "ft.dd1", np, mode, &dd[1]));
-    TRY(fmat(h, "ft.E", np, mode, &E));
-    TRY(fmat(h, "ft.F1", np, mode, &F1));
-    TRY(fmat(h, "ft.dW", np, mode, &dW));
-    TRY(fmat(h, "ft.G1", np, mode, &G1));
-    if (canonical) TRY(fmat(h, "ft.RI", np, mode, &RI));
-    void* ones = nullptr;
-    if (canonical) {
-      TRY(ws(h, "ft.ones", (size_t)N * dsize(dtype), &ones));
-      std::vector<double> h1(N, 1.0);
-      std::vector<float> h1f(N, 1.0f);
-      CK(cudaMemcpyAsync(ones, dtype == SP2_F64 ? (const void*)h1.data() : (const void*)h1f.data(),
-                         (size_t)N * dsize(dtype), cudaMemcpyHostToDevice, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-    }
-    void* trp;
-    TRY(ws(h, "ft.tr", 2 * sizeof(double), &trp));
-    double* tr = static_cast<double*>(trp);
-    const int64_t per = b_diag_only ? N : N * N;
-    const int64_t total = K + (canonical ? 1 : 0);
-    double trI = 0.0;
-    for (int64_t kk = total - 1; kk >= 0; --kk) {  // the response to I first (canonical)
-      const bool isI = canonical && kk == K;
-      const void* src = isI ? ones : static_cast<const char*>(Bd) + (size_t)kk * per * dsize(dtype);
-      const int diag = isI ? 1 : b_diag_only;
-      int cur = 0;
-      FMat& d0 = dd[0];
-      if (mode == SP2_MODE_FP16X2) CK(cudaMemsetAsync(d0.amax, 0, sizeof(float), h->stream));
-      CK(launch_init(src, N, np, 1, dtype, diag, 0, 0.0, -cst, mode, d0.m, nullptr, 0,
-                     mode == SP2_MODE_FP16X2 ? d0.amax : nullptr, h->stream));
-      c.kernels++;
-      if (mode == SP2_MODE_FP16X2) TRY(fplanes(c, d0));
-      for (int j = 0; j < n; ++j) {
-        FMat& din = dd[cur];
-        FMat& dout = (j == n - 1 && isI) ? RI : dd[1 - cur];
-        // E = d delta delta + delta d delta = Z1 + Z1^T, Z1 = d delta * delta
-        TRY(fprod(c, P, din, dl[j]));
-        TRY(fcomb(c, E, &P, 1.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
-        // dW = -4 W E W = -2 (F2 + F2^T), F2 = (W E) W
-        TRY(fprod(c, F1, W[j], E));
-        TRY(fplanes(c, F1));
-        TRY(fprod(c, U, F1, W[j]));
-        TRY(fcomb(c, dW, &U, -2.0, nullptr, 0.0, nullptr, 0.0, 0.0, true));
-        // d delta' = 2 (d delta W + delta dW) = (G1 + G1^T) + (G2 + G2^T)
-        TRY(fprod(c, G1, din, W[j]));
-        TRY(fprod(c, T, dl[j], dW));
-        TRY(fcomb(c, dout, &G1, 1.0, &T, 1.0, nullptr, 0.0, 0.0, j < n - 1));
-        cur = 1 - cur;
-      }
-      if (isI) {
-        CK(launch_trace(mode, RI.m.master, np, N, tr + 1, h->stream));
-        CK(cudaMemcpyAsync(&h->h_state->bounds[1], tr + 1, sizeof(double), cudaMemcpyDeviceToHost,
-                           h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        trI = h->h_state->bounds[1];
-        c.kernels++;
-        continue;
-      }
-      FMat& res = dd[cur];
-      FMat* outm = &res;
-      if (canonical) {
-        CK(launch_trace(mode, res.m.master, np, N, tr, h->stream));
-        CK(cudaMemcpyAsync(&h->h_state->bounds[0], tr, sizeof(double), cudaMemcpyDeviceToHost,
-                           h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        const double trk = h->h_state->bounds[0];
-        c.kernels++;
-        // res - (trk / trI) RI, written as (a/2)(RI + RI^T) + res (RI is exactly symmetric)
-        TRY(fcomb(c, G1, &RI, -0.5 * trk / trI, nullptr, 0.0, &res, 1.0, 0.0, false));
-        outm = &G1;
-      }
-      CK(launch_copy_out(outm->m, N, np, 1, mode, 1.0,
-                         static_cast<char*>(oy.dev) + (size_t)kk * N * N * dsize(dtype), dtype,
-                         h->stream));
-      c.kernels++;
-    }
-    TRY(finish_out(h, oy));
+  const int64_t per = b_diag_only ? N : N * N;
+  for (int64_t kk = K - 1; kk >= 0; --kk) {
+    FMat* r;
+    TRY(fermi_response(c, fs, static_cast<const char*>(Bd) + (size_t)kk * per * dsize(dtype), dtype,
+                       b_diag_only, false, &r));
+    CK(launch_copy_out(r->m, N, np, 1, mode, 1.0,
+                       static_cast<char*>(oy.dev) + (size_t)kk * N * N * dsize(dtype), dtype,
+                       h->stream));
+    c.kernels++;
   }
+  if (K > 0) TRY(finish_out(h, oy));
   CK(cudaStreamSynchronize(h->stream));
   if (info) {
-    info->M = n;
+    info->M = fs.n;
     info->converged = 1;
     info->alpha = 0.5;
-    info->beta = -cst;
-    info->eps_min = emin;
-    info->eps_max = emax;
+    info->beta = -fs.cst;
+    info->eps_min = fs.emin;
+    info->eps_max = fs.emax;
   }
   fill_timing(c, 1 << 30, info);
   return SP2_OK;
@@ -1697,6 +1741,10 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   if (so->mixer == SP2_MIX_MLP && (!so->W1 || !so->W2 || so->hidden < 1))
     return fail(h, SP2_EINVAL, "MLP mixer needs W1, W2 and hidden");
   if (so->mixer < 0 || so->mixer > 2) return fail(h, SP2_EINVAL, "unknown mixer");
+  const bool finite_t = so->kT > 0.0;
+  const int ndbl = so->n_doublings > 0 ? so->n_doublings : 20;
+  if (finite_t && (!std::isfinite(so->mu) || ndbl > 64))
+    return fail(h, SP2_EINVAL, "finite-T SCF: mu must be finite, n_doublings <= 64");
   sp2_opts o = resolve(opts_in);
   TRY(validate_opts(h, &o));
   const bool refine = so->refine_below > 0.0 && so->refine_mode != o.mode;
@@ -1757,6 +1805,8 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   int it = 0;
   bool done = false;
   std::vector<double> Gh, ch;
+  FermiState fs;               // finite T: the recursion's history, set up once per arithmetic
+  if (finite_t) TRY(fermi_setup(c, fs, Hd, N, dtype, so->mu, so->kT, ndbl, so->canonical != 0, true));
   std::vector<int8_t> frozen;  // branch signs of the SP2 run that fixed the polynomial
   bool frozen_here = false;    // the fixed polynomial is this loop's (not the caller's)
   int a0 = 0;                  // first iteration of the current Anderson history
@@ -1769,6 +1819,16 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
                              ns, u, h->stream));
     CK(launch_expand_sites(u, F, ns, norb, pub, dtype, h->stream));
     c.kernels += 2;
+    if (finite_t) {
+      // one finite-temperature response per field through the kept history
+      const size_t per = (size_t)N * dsize(dtype);
+      for (int64_t f = 0; f < F; ++f) {
+        FMat* r;
+        TRY(fermi_response(c, fs, static_cast<const char*>(pub) + f * per, dtype, 1, false, &r));
+        CK(launch_site_charges(r->m.master, o.mode, 1, ns, norb, np, qo + f * ns, h->stream));
+        c.kernels++;
+      }
+    } else {
     Sp2Out rr;
     TRY(run_sp2(h, Hd, N, dtype, nocc, o, pub, F, 1, false, X, Y, c, &rr));
     if (!rr.converged) return fail(h, SP2_ENOCONV, "SP2 did not converge inside the SCF loop");
@@ -1785,6 +1845,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       o.eps_max = rr.emax;
     }
     CK(launch_site_charges(Y[rr.yslot].master, o.mode, F, ns, norb, np, qo, h->stream));
+    }
     CK(cudaMemsetAsync(norms, 0, 2 * sizeof(double), h->stream));
     CK(launch_residual(qo, q, tot, r, norms, h->stream));
     c.kernels += 2;
@@ -1821,6 +1882,8 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
         o.sigma_in = nullptr;
         o.eps_min = o.eps_max = 0.0;
       }
+      if (finite_t)
+        TRY(fermi_setup(c, fs, Hd, N, dtype, so->mu, so->kT, ndbl, so->canonical != 0, true));
       refine_iter = it + 1;
       a0 = it + 1;  // the new Anderson history holds only residuals of the refined arithmetic
       since_best = 0;

@@ -98,6 +98,32 @@ def test_scf_dual_on_gpu(pkg, small):
     assert rel(primal, exact_) < 1e-8 and rel(dual, exact_) < 1e-8
 
 
+def test_scf_finite_temperature(pkg, small):
+    """Self-consistent response at finite temperature (Sec. V.B responses with
+    the canonical mu_1 inside Eq. DM_CP_SCF) against the oracle's exact linear
+    solve with the finite-T site susceptibility, FP64; and Eq. CP_SCF at finite
+    T: primal (per field) and dual (per observable) agree."""
+    tb, chi0, K, Vx = small
+    e, V = exact.eigh(tb.H)
+    mu = 0.5 * (e[tb.nocc - 1] + e[tb.nocc])
+    kT = 0.05
+    c0 = scf.chi0_sites_fermi(e, V, mu, kT, tb.norb, canonical=True)
+    H = torch.from_numpy(tb.H).cuda()
+    kw = dict(mixer="anderson", alpha=0.3, tol=1e-11, max_iter=200, mode="fp64", kT=kT, mu=mu,
+              n_doublings=24)
+    q, res, its, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, Vx, **kw)
+    assert res[-1] <= 1e-11
+    assert rel(q, scf.scf_exact(c0, K, Vx)) < 1e-7
+    obs = np.ascontiguousarray((tb.pos - 0.5 * tb.box).T)
+    q_a, _, _, _ = pkg.sp2_scf_response(H, tb.nocc, 4, K, obs, **kw)
+    assert rel(q_a @ Vx.T, obs @ q.T) < 1e-9
+    q16, res16, _, _ = pkg.sp2_scf_response(H.float(), tb.nocc, 4, K, Vx, mixer="anderson",
+                                            tol=1e-5, max_iter=100, mode="fp16x2", kT=kT, mu=mu,
+                                            n_doublings=24)
+    assert res16[-1] <= 1e-5
+    assert rel(q16, scf.scf_exact(c0, K, Vx)) < 1e-3
+
+
 def test_mlp_kernels_against_oracle(pkg):
     rng = np.random.default_rng(0)
     din, dh, P = 96, 40, 70

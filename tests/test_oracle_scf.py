@@ -110,3 +110,33 @@ def test_scf_dual_equals_primal(small):
     # the non-self-consistent limit K = 0 is the plain symmetry of chi0
     Z = np.zeros_like(K)
     assert np.allclose(obs @ scf.scf_exact(chi0, Z, Vx).T, (obs @ chi0) @ Vx.T, rtol=1e-10)
+
+
+def test_finite_t_chi0_and_scf_duality(small):
+    """Finite-temperature site susceptibility (canonical): symmetric, charge
+    conserving (a uniform potential moves no charge: Tr[D1] = 0 by mu_1), equal
+    to central differences of the Fermi-Dirac site charges at fixed electron
+    count, and the self-consistent duality a . q*(V) = q*(a) . V holds."""
+    from oracle import exact
+    tb, e, V, chi0, K, Vx = small
+    mu = 0.5 * (e[tb.nocc - 1] + e[tb.nocc])
+    kT = 0.05
+    c0 = scf.chi0_sites_fermi(e, V, mu, kT, tb.norb, canonical=True)
+    assert np.allclose(c0, c0.T, atol=1e-12)
+    assert np.allclose(c0.sum(axis=0), 0.0, atol=1e-10)
+    # grand canonical: central differences of the site charges at fixed mu
+    cg = scf.chi0_sites_fermi(e, V, mu, kT, tb.norb, canonical=False)
+    h = 1e-5
+    b = 5
+    P = np.zeros(tb.n)
+    P[b * 4:(b + 1) * 4] = 1.0
+
+    def q(t):
+        ee, VV = exact.eigh(tb.H + t * np.diag(P))
+        D = (VV * exact.fermi(ee, mu, kT)[None, :]) @ VV.T
+        return np.diag(D).reshape(-1, 4).sum(axis=1)
+    assert np.allclose(cg[:, b], (q(h) - q(-h)) / (2 * h), rtol=1e-6, atol=1e-9)
+    obs = (tb.pos - 0.5 * tb.box).T.copy()
+    primal = obs @ scf.scf_exact(c0, K, Vx).T
+    dual = scf.scf_exact(c0, K, obs) @ Vx.T
+    assert np.allclose(primal, dual, rtol=1e-10, atol=1e-12 * np.abs(primal).max())
