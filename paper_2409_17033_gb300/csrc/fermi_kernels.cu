@@ -11,49 +11,105 @@ __device__ __forceinline__ void atomic_max_nonneg_f(float* addr, float v) {
 }
 
 // out = z1 (Z1 + Z1^T) + z2 (Z2 + Z2^T) + a A + id I (I restricted to the
-// caller's n x n block). Null operands are skipped. One block per 32 x 32
-// tile pair (I <= J); both tiles written, each element from its own inputs.
+// caller's n x n block). Null operands are skipped. One block of 256 threads per
+// upper-triangle tile pair (I <= J) of TE x TE tiles, from a linear block index;
+// both tiles written with 16-byte accesses, each element from its own inputs.
 template <typename T>
-__global__ void k_combine(T* __restrict__ out, int64_t np, int64_t n, const T* __restrict__ Z1,
-                          T z1, const T* __restrict__ Z2, T z2, const T* __restrict__ A, T a,
-                          T id, float* amax) {
-  const int I = blockIdx.y, J = blockIdx.x;
-  if (I > J) return;
-  __shared__ T s1a[32][33], s1b[32][33], s2a[32][33], s2b[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int k = 0; k < 32; k += 8) {
-    const int r = ty + k;
-    const int64_t ij = (int64_t)(I * 32 + r) * np + J * 32 + tx;
-    const int64_t ji = (int64_t)(J * 32 + r) * np + I * 32 + tx;
-    if (Z1) {
-      s1a[r][tx] = Z1[ij];
-      s1b[r][tx] = Z1[ji];
+constexpr int comb_tile() { return sizeof(T) == 4 ? 64 : 32; }
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_combine(T* __restrict__ out, int64_t np, int64_t n, const T* __restrict__ Z1, T z1,
+              const T* __restrict__ Z2, T z2, const T* __restrict__ A, T a, T id, float* amax) {
+  constexpr int TE = comb_tile<T>();
+  constexpr int V = TE / 4, R = 256 / V, P = TE / R;
+  const int64_t t = blockIdx.x;
+  int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (J * (J + 1) / 2 > t) --J;
+  while ((J + 1) * (J + 2) / 2 <= t) ++J;
+  const int64_t I = t - J * (J + 1) / 2;
+  const bool diag = I == J;
+  __shared__ T sa[TE][TE + 1], sb[TE][TE + 1];
+  const int c4 = (threadIdx.x % V) * 4, r0 = threadIdx.x / V;
+  const int64_t rI = I * TE, rJ = J * TE;
+  T v[P][4], w[P][4];   // out tile (I,J) and, off the diagonal, tile (J,I)
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[p][j] = w[p][j] = (T)0;
+  for (int op = 0; op < 2; ++op) {
+    const T* Z = op == 0 ? Z1 : Z2;
+    const T zc = op == 0 ? z1 : z2;
+    if (!Z) continue;   // uniform across the block
+    __syncthreads();    // the previous operand's tiles are no longer read
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int r = r0 + p * R;
+      T x[4], y[4];
+      ld4(Z + (rI + r) * np + rJ + c4, x);
+      ld4(Z + (rJ + r) * np + rI + c4, y);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sa[r][c4 + j] = x[j], sb[r][c4 + j] = y[j];
     }
-    if (Z2) {
-      s2a[r][tx] = Z2[ij];
-      s2b[r][tx] = Z2[ji];
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int r = r0 + p * R;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        v[p][j] += zc * (sa[r][c4 + j] + sb[c4 + j][r]);
+        w[p][j] += zc * (sb[r][c4 + j] + sa[c4 + j][r]);
+      }
     }
   }
-  __syncthreads();
   float m = 0.0f;
-  for (int pass = 0; pass < (I == J ? 1 : 2); ++pass) {
-    const int R0 = pass == 0 ? I : J, C0 = pass == 0 ? J : I;
-    for (int k = 0; k < 32; k += 8) {
-      const int r = ty + k, c = tx;
-      const int64_t gi = (int64_t)R0 * 32 + r, gj = (int64_t)C0 * 32 + c;
-      const int64_t idx = gi * np + gj;
-      T v = (T)0;
-      if (Z1) v += z1 * (pass == 0 ? s1a[r][c] + s1b[c][r] : s1b[r][c] + s1a[c][r]);
-      if (Z2) v += z2 * (pass == 0 ? s2a[r][c] + s2b[c][r] : s2b[r][c] + s2a[c][r]);
-      if (A) v += a * A[idx];
-      if (gi == gj && gi < n) v += id;
-      out[idx] = v;
-      m = fmaxf(m, fabsf((float)v));
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int r = r0 + p * R;
+    for (int pass = 0; pass < (diag ? 1 : 2); ++pass) {
+      const int64_t gi = (pass == 0 ? rI : rJ) + r, gj0 = (pass == 0 ? rJ : rI) + c4;
+      T o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = pass == 0 ? v[p][j] : w[p][j];
+      if (A) {
+        T x[4];
+        ld4(A + gi * np + gj0, x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] += a * x[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (gi == gj0 + j && gi < n) o[j] += id;
+        m = fmaxf(m, fabsf((float)o[j]));
+      }
+      st4(out + gi * np + gj0, o);
     }
   }
   if (amax) {
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (tx == 0 && m > 0.0f) atomic_max_nonneg_f(amax, m);
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomic_max_nonneg_f(amax, m);
   }
 }
 
@@ -78,7 +134,9 @@ __global__ void k_trace(const T* __restrict__ M, int64_t np, int64_t n, double* 
 cudaError_t launch_combine(int mode, void* out, int64_t np, int64_t n, const void* Z1, double z1,
                            const void* Z2, double z2, const void* A, double a, double id,
                            float* amax, cudaStream_t s) {
-  dim3 grid((unsigned)(np / 32), (unsigned)(np / 32)), block(32, 8);
+  // np is a multiple of 256, so both tile edges divide it
+  const int64_t nb = np / (mode == SP2_MODE_FP64 ? comb_tile<double>() : comb_tile<float>());
+  const dim3 grid((unsigned)(nb * (nb + 1) / 2)), block(256);
   if (mode == SP2_MODE_FP64)
     k_combine<double><<<grid, block, 0, s>>>(
         static_cast<double*>(out), np, n, static_cast<const double*>(Z1), z1,

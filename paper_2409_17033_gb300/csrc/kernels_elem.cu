@@ -380,22 +380,28 @@ __global__ void k_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int
   }
 }
 
+// planes of four consecutive entries (8-byte stores per plane)
+__device__ __forceinline__ uint2 pack4(const uint16_t (&v)[4]) {
+  return make_uint2(v[0] | ((uint32_t)v[1] << 16), v[2] | ((uint32_t)v[3] << 16));
+}
+
+// hi/lo (and BF16X3 mid) planes from the FP32 master; total is a multiple of 4
 __global__ void k_split(MatBuf m, int64_t total, int mode) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+  const int64_t total4 = total / 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total4;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const float f = static_cast<const float*>(m.master)[t];
-    uint16_t h, l;
-    if (mode == SP2_MODE_BF16X3) {
-      uint16_t md;
-      split_bf16x3(f, h, md, l);
-      m.mid[t] = md;
-    } else if (mode == SP2_MODE_BF16X2) {
-      split_bf16(f, h, l);
-    } else {
-      split_fp16(f, 1.0f, h, l);
+    const float4 f = reinterpret_cast<const float4*>(m.master)[t];
+    const float x[4] = {f.x, f.y, f.z, f.w};
+    uint16_t h[4], l[4], md[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (mode == SP2_MODE_BF16X3) split_bf16x3(x[j], h[j], md[j], l[j]);
+      else if (mode == SP2_MODE_BF16X2) split_bf16(x[j], h[j], l[j]);
+      else split_fp16(x[j], 1.0f, h[j], l[j]);
     }
-    m.hi[t] = h;
-    m.lo[t] = l;
+    reinterpret_cast<uint2*>(m.hi)[t] = pack4(h);
+    reinterpret_cast<uint2*>(m.lo)[t] = pack4(l);
+    if (mode == SP2_MODE_BF16X3) reinterpret_cast<uint2*>(m.mid)[t] = pack4(md);
   }
 }
 
@@ -404,15 +410,20 @@ __global__ void k_scales_from_max(ScaleBuf sc, int slot) {
     sc.yscale[slot * sc.B + b] = pow2_scale(sc.ymax[slot * sc.B + b]);
 }
 
+// FP16X2 planes of a batch of sc.B matrices of `per` entries each (per % 4 == 0),
+// each with its slot's power-of-two scale
 __global__ void k_split_scaled(MatBuf m, int64_t per, ScaleBuf sc, int slot) {
-  const int64_t total = per * sc.B;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+  const int64_t total4 = per * sc.B / 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total4;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const float f = static_cast<const float*>(m.master)[t];
-    uint16_t h, l;
-    split_fp16(f, sc.yscale[slot * sc.B + t / per], h, l);
-    m.hi[t] = h;
-    m.lo[t] = l;
+    const float4 f = reinterpret_cast<const float4*>(m.master)[t];
+    const float x[4] = {f.x, f.y, f.z, f.w};
+    const float scale = sc.yscale[slot * sc.B + (4 * t) / per];
+    uint16_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) split_fp16(x[j], scale, h[j], l[j]);
+    reinterpret_cast<uint2*>(m.hi)[t] = pack4(h);
+    reinterpret_cast<uint2*>(m.lo)[t] = pack4(l);
   }
 }
 
@@ -583,13 +594,13 @@ cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, in
 }
 
 cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, int mode, cudaStream_t s) {
-  k_split<<<grid_for(rows * np, 256, 8192), 256, 0, s>>>(m, rows * np, mode);
+  k_split<<<grid_for(rows * np / 4, 256, 8192), 256, 0, s>>>(m, rows * np, mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_split_scaled(MatBuf m, int64_t np, ScaleBuf sc, int slot, cudaStream_t s) {
   k_scales_from_max<<<1, 256, 0, s>>>(sc, slot);
-  k_split_scaled<<<grid_for(sc.B * np * np, 256, 8192), 256, 0, s>>>(m, np * np, sc, slot);
+  k_split_scaled<<<grid_for(sc.B * np * np / 4, 256, 8192), 256, 0, s>>>(m, np * np, sc, slot);
   return cudaGetLastError();
 }
 
