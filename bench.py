@@ -396,6 +396,9 @@ def run_ours(args, ws, rank):
         hh = sp2.Handle()
         kwh = dict(kw)
         kwh["handle"] = hh
+        # page-locked result buffers, as a user streaming results to the host would pass
+        kwh["out"] = torch.empty((1, n, n), dtype=torch.float32).pin_memory().numpy()
+        kwh["D_out"] = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
         sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
         barrier(ws)
         t0 = time.perf_counter()

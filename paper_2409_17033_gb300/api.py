@@ -180,15 +180,19 @@ def sp2_response(H, nocc: float, H1, diag_only: bool = False, mode="bf16x2",
 
 def sp2_susceptibility(H, nocc: float, A, direction: str = "forward", diag_only: bool = False,
                        mode="bf16x2", want_density: bool = False, handle: Handle | None = None,
-                       allow_noconv: bool = False, **kw):
+                       allow_noconv: bool = False, out=None, D_out=None, **kw):
     """chi^A_l for observables A_l (L, N, N) or diagonals (L, N): forward
-    Eq. DMSuscept, or backward Eq. DM2 with checkpointed X_n. Returns (chi, D or None, info)."""
+    Eq. DMSuscept, or backward Eq. DM2 with checkpointed X_n. Returns (chi, D or None, info).
+    out / D_out: caller-owned result arrays (L, N, N) / (N, N) of H's dtype and kind,
+    e.g. page-locked host memory for fast device-to-host copies."""
     h = handle or default_handle()
     h.bind_stream()
     n = H.shape[0]
     l = A.shape[0]
-    chi = _empty_like(H, (l, n, n))
-    D = _empty_like(H, (n, n)) if want_density else None
+    chi = out if out is not None else _empty_like(H, (l, n, n))
+    D = (D_out if D_out is not None else _empty_like(H, (n, n))) if want_density else None
+    if tuple(chi.shape) != (l, n, n) or (D is not None and tuple(D.shape) != (n, n)):
+        raise ValueError("out / D_out have the wrong shape")
     opts, _keep = make_opts(mode, **kw)
     info = L.Info()
     d = {"forward": 0, "backward": 1}[direction]

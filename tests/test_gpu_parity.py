@@ -345,6 +345,13 @@ def test_host_buffers_match_device_buffers(sp2, c1):
     assert isinstance(chi_h, np.ndarray)
     assert np.array_equal(chi_h, chi_d.cpu().numpy())
     assert np.array_equal(D_h, D_d.cpu().numpy())
+    # caller-owned page-locked result buffers receive the same values
+    out = torch.empty((1, 128, 128), dtype=torch.float32).pin_memory().numpy()
+    Dout = torch.empty((128, 128), dtype=torch.float32).pin_memory().numpy()
+    chi_p, D_p, _ = sp2.sp2_susceptibility(Hh, p.nocc, Ah, "backward", mode="bf16x2",
+                                           want_density=True, out=out, D_out=Dout)
+    assert chi_p is out and D_p is Dout
+    assert np.array_equal(out, chi_h) and np.array_equal(Dout, D_h)
 
 
 def test_response_contract_dense_and_diagonal(sp2):
