@@ -36,6 +36,13 @@ Readings where the paper is silent (the same readings the CUDA path takes):
     exceed the true error of the slow near-gap eigenvalues, whereas f
     weights every eigenvalue by its squared error. ``max_iter`` steps
     without any test firing is non-convergence.
+  * result at the floor: when a floor test fires, the result is the iterate
+    X_{n*} with the smallest f among those with f <= floor_gate (n* >= 2),
+    i.e. M = n* - 1 steps, not the last one formed. Past the floor, rounding
+    makes f cycle (it grows about fourfold per 2X - X^2 step until a squaring
+    resets it), and the response's near-gap terms follow that cycle: the
+    error of chi against the exact form tracks sqrt(f) of the returned
+    iterate. The tolerance test returns the last iterate as before.
 """
 from __future__ import annotations
 
@@ -87,24 +94,35 @@ def idem_fro(X: np.ndarray, X2: np.ndarray) -> float:
 
 
 def stop_now(n: int, e: list[float], f: list[float], sig: list[int], idem_tol: float,
-             floor_gate: float, min_iter: int) -> bool:
+             floor_gate: float, min_iter: int) -> int:
     """Stopping reading (module docstring). ``e[k]`` is the trace error of
     X_{k+1} (after step n the newest is e[n], of X_{n+1}); ``f[k]`` is the
     squared Frobenius error of X_{k+1} (after step n the newest is f[n-1], of
-    X_n); ``sig[k]`` is sigma_{k+1}."""
+    X_n); ``sig[k]`` is sigma_{k+1}. Returns 0 (go on), 1 (tolerance test) or
+    2 (a precision-floor test)."""
     if n < min_iter:
-        return False
+        return 0
     if idem_tol > 0.0 and abs(e[n]) <= idem_tol:
-        return True
+        return 1
     if floor_gate <= 0.0:
-        return False
+        return 0
     if n >= 3 and sig[n - 3] != sig[n - 2] and f[n - 3] <= floor_gate and f[n - 1] >= f[n - 3]:
-        return True
+        return 2
     if n > STALL:
         best = min(f[:n - STALL])
         if best <= floor_gate and min(f[n - STALL:n]) >= best:
-            return True
-    return False
+            return 2
+    return 0
+
+
+def floor_best(f: list[float], floor_gate: float) -> int:
+    """n* = the index (1-based, >= 2) of the iterate X_{n*} with the smallest f
+    among those with f <= floor_gate, from f[k] = f of X_{k+1}; 0 if none."""
+    best, nb = None, 0
+    for k in range(1, len(f)):
+        if f[k] <= floor_gate and (best is None or f[k] < best):
+            best, nb = f[k], k + 1
+    return nb
 
 
 @dataclasses.dataclass
@@ -117,6 +135,7 @@ class SP2Result:
     fro: list[float]              # f for X_1..X_M
     X: list[np.ndarray] | None    # X_1..X_M (inputs of each step) when kept
     converged: bool
+    stop_step: int = 0            # the step after which a stop test fired (>= M)
 
     @property
     def M(self) -> int:
@@ -144,23 +163,34 @@ def sp2_density(H: np.ndarray, nocc: float, idem_tol: float = 1e-10,
     hist: list[np.ndarray] | None = [] if keep else None
     converged = False
     steps = len(sigma) if sigma is not None else max_iter
+    kept: dict[int, np.ndarray] = {}          # X_n of the floor candidates
     for n in range(1, steps + 1):
         s = sigma[n - 1] if sigma is not None else choose_sigma(t1, t2, nocc)
         if keep:
             hist.append(X)
         X2 = X @ X
         fro.append(idem_fro(X, X2))
+        if sigma is None and fro[-1] <= floor_gate:
+            kept[n] = X
         X = X2 if s > 0 else 2.0 * X - X2
         sig.append(int(s))
         t1, t2 = traces(X)
         errs.append(t1 - t2)
-        if sigma is None and stop_now(n, errs, fro, sig, idem_tol, floor_gate, min_iter):
+        why = stop_now(n, errs, fro, sig, idem_tol, floor_gate, min_iter) if sigma is None else 0
+        if why:
             converged = True
+            nb = floor_best(fro, floor_gate) if why == 2 else 0
+            if nb >= 2 and nb - 1 < n:
+                m = nb - 1                       # return X_{n*}: M = n* - 1 steps
+                X = kept[nb]
+                sig, errs, fro = sig[:m], errs[:m + 1], fro[:m]
+                if keep:
+                    hist = hist[:m]
             break
     if sigma is not None:
         converged = True
     return SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs, fro=fro,
-                     X=hist, converged=converged)
+                     X=hist, converged=converged, stop_step=n if steps > 0 else 0)
 
 
 # ---------------------------------------------------------------- Sec. III
@@ -224,17 +254,27 @@ def merged_response(H: np.ndarray, nocc: float, B: np.ndarray, **kw):
     sig: list[int] = []
     converged = sigma is not None
     steps = len(sigma) if sigma is not None else max_iter
+    kept: dict[int, tuple] = {}              # (X_n, Y_n) of the floor candidates
     for n in range(1, steps + 1):
         s = sigma[n - 1] if sigma is not None else choose_sigma(t1, t2, nocc)
+        Yn = Y
         Y = [_response_step(y, X, s) for y in Y]
         X2 = X @ X
         fro.append(idem_fro(X, X2))
+        if sigma is None and fro[-1] <= floor_gate:
+            kept[n] = (X, Yn)
         X = X2 if s > 0 else 2.0 * X - X2
         sig.append(int(s))
         t1, t2 = traces(X)
         errs.append(t1 - t2)
-        if sigma is None and stop_now(n, errs, fro, sig, idem_tol, floor_gate, min_iter):
+        why = stop_now(n, errs, fro, sig, idem_tol, floor_gate, min_iter) if sigma is None else 0
+        if why:
             converged = True
+            nb = floor_best(fro, floor_gate) if why == 2 else 0
+            if nb >= 2 and nb - 1 < n:
+                m = nb - 1
+                X, Y = kept[nb]
+                sig, errs, fro = sig[:m], errs[:m + 1], fro[:m]
             break
     res = SP2Result(D=X, alpha=alpha, beta=beta, sigma=sig, errors=errs, fro=fro,
                     X=None, converged=converged)

@@ -260,3 +260,27 @@ def test_tight_binding_gap_and_sp2(tmp_path):
     r = sp2.sp2_density(tb.H, tb.nocc, idem_tol=1e-10)
     assert r.converged
     assert rel(r.D, exact.density_zero_T(e, V, tb.nocc)) < 1e-10
+
+
+def test_floor_best_index():
+    """floor_best: the smallest f at or below the gate, from X_2 on, 1-based."""
+    f = [0.5, 0.02, 1e-6, 3e-9, 4e-8, 1e-9, 2e-8]
+    assert sp2.floor_best(f, 0.03) == 6           # f[5] = 1e-9 is X_6
+    assert sp2.floor_best([0.5, 0.2], 0.03) == 0
+    assert sp2.floor_best([1e-9, 0.5, 0.01], 0.03) == 3   # X_1 is never chosen
+
+
+def test_floor_stop_returns_best_iterate(cfg1):
+    """With the tolerance test off, FP64 reaches its rounding floor; the run
+    returns the floor candidate with the smallest f among X_2..X_s (s the step
+    at which the floor test fired), and that iterate replays exactly from its
+    own branch sequence."""
+    p = cfg1
+    r = sp2.sp2_density(p.H, p.nocc, idem_tol=0.0)
+    assert r.converged and r.stop_step >= r.M
+    long = sp2.sp2_density(p.H, p.nocc, idem_tol=0.0, floor_gate=0.0, max_iter=r.stop_step)
+    cand = [(f, k + 1) for k, f in enumerate(long.fro) if k >= 1 and f <= 0.03]
+    assert r.M + 1 == min(cand)[1]
+    replay = sp2.sp2_density(p.H, p.nocc, sigma=r.sigma)
+    assert np.array_equal(replay.D, r.D)
+    assert sp2.idem_fro(r.D, r.D @ r.D) <= 1e-20
