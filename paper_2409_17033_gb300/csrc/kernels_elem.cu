@@ -195,13 +195,20 @@ __global__ void k_decide(const Part3* part, DevState* st, DecideParams p) {
     return;
   }
   const int s = n - 1;  // the step that produced X_n (0 for X_1)
+  // floor candidates: X_s (f known now) with f <= gate and the smallest f so far
+  if (p.fixed_m == 0 && p.floor_gate > 0.0 && s >= 2 && st->f[s] <= p.floor_gate &&
+      (st->nbest == 0 || st->f[s] < st->fbest)) {
+    st->fbest = st->f[s];
+    st->nbest = s;
+    st->keep_step = s;
+  }
   if (p.fixed_m > 0) {
     if (s == p.fixed_m) st->stop_at = s;
     return;  // branches preset by the host
   }
   if (s >= 1 && s >= p.min_iter) {
     const double e = fabs(t1 - t2);
-    bool stop = false;
+    bool stop = false, floor_stop = false;
     if (p.idem_tol > 0.0 && e <= p.idem_tol) stop = true;
     // precision floor on f (see the stop rule in sp2.h):
     //   opposite branches at steps s-2, s-1, f_{s-2} <= gate and f_s >= f_{s-2}; or
@@ -209,22 +216,46 @@ __global__ void k_decide(const Part3* part, DevState* st, DecideParams p) {
     if (!stop && p.floor_gate > 0.0) {
       if (s >= 3 && st->sigma[s - 2] != st->sigma[s - 1] && st->f[s - 2] <= p.floor_gate &&
           st->f[s] >= st->f[s - 2])
-        stop = true;
-      if (!stop && s > kStall) {
+        floor_stop = true;
+      if (!floor_stop && s > kStall) {
         double best = st->f[1];
         for (int k = 2; k <= s - kStall; ++k) best = fmin(best, st->f[k]);
         double recent = st->f[s - kStall + 1];
         for (int k = s - kStall + 2; k <= s; ++k) recent = fmin(recent, st->f[k]);
-        if (best <= p.floor_gate && recent >= best) stop = true;
+        if (best <= p.floor_gate && recent >= best) floor_stop = true;
       }
+      if (floor_stop) stop = true;
     }
     if (stop) {
-      st->stop_at = s;
+      st->stop_step = s;
+      // at the floor the result is the kept candidate X_nbest (M = nbest - 1 steps)
+      if (floor_stop && st->nbest >= 2 && st->nbest - 1 < s) {
+        st->stop_at = st->nbest - 1;
+        st->backtracked = 1;
+      } else {
+        st->stop_at = s;
+      }
       return;
     }
   }
   // Eq. DM0 branch: the trace after X^2 is t2, after 2X - X^2 it is 2 t1 - t2.
   st->sigma[n] = (fabs(t2 - p.nocc) <= fabs(2.0 * t1 - t2 - p.nocc)) ? 1 : -1;
+}
+
+template <typename T>
+__global__ void k_keep_best(const T* __restrict__ src, T* __restrict__ dst, int64_t count,
+                            const DevState* st, int step) {
+  if (*((volatile const int*)&st->keep_step) != step) return;
+  const int64_t n4 = count / 4;   // count is a multiple of np^2, np % 256 == 0
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) {
+      reinterpret_cast<float4*>(dst)[t] = reinterpret_cast<const float4*>(src)[t];
+    } else {
+      reinterpret_cast<double2*>(dst)[2 * t] = reinterpret_cast<const double2*>(src)[2 * t];
+      reinterpret_cast<double2*>(dst)[2 * t + 1] = reinterpret_cast<const double2*>(src)[2 * t + 1];
+    }
+  }
 }
 
 __device__ __forceinline__ bool halted(const DevState* st, int step) {
@@ -554,6 +585,18 @@ cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, i
   int grid = part ? nparts : grid_for(batch * np, 1, 4096);
   k_init<<<grid, kRedThreads, 0, s>>>(src, n, np, batch, dtype, diag_only, symmetrize, alpha,
                                       beta, mode, dst, part, ymax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keep_best(const void* src, void* dst, int64_t count, int mode, const DevState* st,
+                             int step, cudaStream_t s) {
+  const int grid = 2 * 152 * 4;
+  if (mode == SP2_MODE_FP64)
+    k_keep_best<double><<<grid, 256, 0, s>>>(static_cast<const double*>(src),
+                                             static_cast<double*>(dst), count, st, step);
+  else
+    k_keep_best<float><<<grid, 256, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst),
+                                            count, st, step);
   return cudaGetLastError();
 }
 

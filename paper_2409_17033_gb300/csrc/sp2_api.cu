@@ -452,8 +452,9 @@ struct Sp2Out {
   int M = 0;
   bool converged = false;
   double alpha = 0, beta = 0, emin = 0, emax = 0;
-  int xslot = 0;  // buffer holding X_{M+1}
-  int yslot = 0;  // buffer holding Y_{M+1}
+  MatBuf xout;    // X_{M+1} (the kept floor candidate when the stop backtracked: master only)
+  MatBuf yout;    // Y_{M+1}, likewise
+  int stop_step = 0;  // the step after which the stop test fired (>= M)
 };
 
 // Runs Eq. DM0 on the padded X_1 = alpha I + beta H. If ybatch > 0, the
@@ -542,6 +543,13 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   const int64_t l0 = c.launches;
   double fstep = 0.0, astep = 0.0;
   int64_t lstep = 0;
+  // the floor candidate with the smallest f so far (the result when the floor test fires)
+  const bool track = o.floor_gate > 0.0 && o.fixed_m == 0;
+  MatBuf xbest, ybest;
+  if (track) {
+    TRY(ws(h, "Xbest.m", xbytes, &xbest.master));
+    if (ybatch > 0) TRY(ws(h, "Ybest.m", (size_t)ybatch * xbytes, &ybest.master));
+  }
   for (int step = 1; step <= maxit && !stopped; ++step) {
     const MatBuf& xin = X[step % 2];
     const MatBuf& xo = X[(step + 1) % 2];
@@ -567,6 +575,15 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
     dp.nparts = nparts;
     CK(launch_decide(c.part, c.st, dp, h->stream));
     c.kernels++;
+    if (track) {
+      CK(launch_keep_best(xin.master, xbest.master, np * np, mode, c.st, step, h->stream));
+      c.kernels++;
+      if (ybatch > 0) {
+        CK(launch_keep_best(Y[step % 2].master, ybest.master, ybatch * np * np, mode, c.st, step,
+                            h->stream));
+        c.kernels++;
+      }
+    }
     if (step == 1) {
       fstep = c.flops - f0;
       astep = c.alg - a0;
@@ -585,12 +602,15 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   if (!stopped) M = maxit;
   out->M = M;
   out->converged = stopped;
-  out->xslot = (M + 1) % 2;
-  out->yslot = (M + 1) % 2;
+  const bool back = stopped && h->h_state->backtracked;
+  out->xout = back ? xbest : X[(M + 1) % 2];
+  out->yout = back ? ybest : Y[(M + 1) % 2];
+  out->stop_step = stopped ? h->h_state->stop_step : M;
+  if (out->stop_step < M) out->stop_step = M;
   // executed-work accounting covers only the steps that ran (later launches were no-ops)
-  c.flops = f0 + fstep * M;
-  c.alg = a0 + astep * M;
-  c.launches = l0 + lstep * M;
+  c.flops = f0 + fstep * out->stop_step;
+  c.alg = a0 + astep * out->stop_step;
+  c.launches = l0 + lstep * out->stop_step;
   return SP2_OK;
 }
 
@@ -926,7 +946,7 @@ int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc
     TRY(resolve_ckpt(h, &o, np, 1));
   }
   TRY(run_sp2(h, Hd, N, dtype, nocc, o, nullptr, 0, 0, keep, X, Y, c, &r));
-  CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
+  CK(launch_copy_out(r.xout, N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
   c.kernels++;
   TRY(finish_out(h, od));
   CK(cudaStreamSynchronize(h->stream));
@@ -977,12 +997,12 @@ int sp2_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double noc
   Sp2Out r;
   TRY(run_sp2(h, Hd, N, dtype, nocc, o, Bd, K, h1_diag_only, false, X, Y, c, &r));
   if (D) {
-    CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
+    CK(launch_copy_out(r.xout, N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
     c.kernels++;
     TRY(finish_out(h, od));
   }
   if (K > 0) {
-    CK(launch_copy_out(Y[r.yslot], N, np, K, o.mode, 1.0, oy.dev, dtype, h->stream));
+    CK(launch_copy_out(r.yout, N, np, K, o.mode, 1.0, oy.dev, dtype, h->stream));
     c.kernels++;
     TRY(finish_out(h, oy));
   }
@@ -1029,7 +1049,7 @@ int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, doub
   TRY(resolve_ckpt(h, &o, np, L));
   TRY(run_sp2(h, Hd, N, dtype, nocc, o, nullptr, 0, 0, true, X, Y, c, &r));
   if (D) {
-    CK(launch_copy_out(X[r.xslot], N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
+    CK(launch_copy_out(r.xout, N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
     c.kernels++;
     TRY(finish_out(h, od));
   }
@@ -1844,7 +1864,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       o.eps_min = rr.emin;
       o.eps_max = rr.emax;
     }
-    CK(launch_site_charges(Y[rr.yslot].master, o.mode, F, ns, norb, np, qo, h->stream));
+    CK(launch_site_charges(rr.yout.master, o.mode, F, ns, norb, np, qo, h->stream));
     }
     CK(cudaMemsetAsync(norms, 0, 2 * sizeof(double), h->stream));
     CK(launch_residual(qo, q, tot, r, norms, h->stream));

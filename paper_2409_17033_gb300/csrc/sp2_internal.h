@@ -31,6 +31,11 @@ struct DevState {
   int abort_flag;                // a device wait timed out (kernel bailed out)
   int pad_;
   double bounds[2];              // Gershgorin eps_min, eps_max
+  double fbest;                  // smallest f among the floor candidates (f <= floor_gate)
+  int nbest;                     // its iterate index n (X_n), 0 if none yet
+  int keep_step;                 // step whose input X_n (and Y_n) is to be kept now
+  int backtracked;               // the floor stop returned X_nbest, not the last iterate
+  int stop_step;                 // the step after which the stop test fired
 };
 
 // Storage of one padded matrix (or a batch of them) in a given mode.
@@ -142,6 +147,10 @@ struct DecideParams {
   int fixed_m;       // > 0: sigma preset, stop when n - 1 == fixed_m
 };
 cudaError_t launch_decide(const Part3* part, DevState* st, DecideParams p, cudaStream_t s);
+// copy `count` entries of the master src -> dst when st->keep_step == step (the
+// floor candidate with the smallest f so far), else nothing
+cudaError_t launch_keep_best(const void* src, void* dst, int64_t count, int mode, const DevState* st,
+                             int step, cudaStream_t s);
 
 // Y_{n+1} = sigma>0 ? Z + Z^T : 2 Y - (Z + Z^T) for a batch; step n reads sigma_n.
 // FP16X2: the planes of Y_{n+1} use the scale bounded by 2 max|Z| (+ 2 max|Y_n|

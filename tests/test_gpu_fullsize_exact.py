@@ -57,6 +57,8 @@ def test_fullsize_against_exact():
               f"rel err D {err[mode][0]:.2e} chi {err[mode][1]:.2e} (host eigh {t_eigh:.0f} s)")
     print(f"N=16384 chi fp16x2 vs bf16x3 {rel(out['fp16x2'][1], out['bf16x3'][1]):.2e}, "
           f"fp16x2 vs fp32 {rel(out['fp16x2'][1], out['fp32'][1]):.2e}")
-    assert err["fp16x2"][0] < 5e-5 and err["bf16x3"][0] < 5e-5
+    # measured: fp16x2 D 7.8e-6 chi 1.15e-2; bf16x3 9.7e-6, 1.2e-2; fp32 2.8e-4, 2.0
+    assert err["fp16x2"][0] < 3e-5 and err["bf16x3"][0] < 3e-5
+    assert err["fp16x2"][1] < 4e-2 and err["bf16x3"][1] < 4e-2
     # the split tensor-core paths are no less accurate than plain FP32 CUDA-core products
     assert err["fp16x2"][1] <= 1.5 * err["fp32"][1]
