@@ -110,7 +110,10 @@ typedef struct {
                           or when the smallest f so far is <= floor_gate and none of the last
                           4 steps went below it. In exact arithmetic neither happens once
                           f <= 0.03 (every eigenvalue is within 1/4 of 0 or 1 and a pair of
-                          opposite branches maps a distance d to at most 4 d^2). */
+                          opposite branches maps a distance d to at most 4 d^2). The result
+                          is then the iterate X_n (n >= 2, f_n <= floor_gate) with the
+                          smallest f_n, so M = n - 1: past the floor f cycles with rounding,
+                          and the near-gap response terms follow it. */
   int max_iter;        /* cap on SP2 steps M (1..SP2_MAX_ITER; 0 = default 100) */
   int min_iter;        /* no stop test before this step (default 4 when < 0) */
   int fixed_m;         /* > 0: take exactly fixed_m steps with the branches in sigma_in */

@@ -16,15 +16,20 @@
 //           columns) combined as acc0 + 2^-11 acc1; A may carry a per-matrix
 //           power-of-two scale that the epilogue divides out.
 //
-// CTA tile 128 x 256, K step 64 (one 128-byte swizzle row of bf16), 4-stage
-// TMA -> shared-memory ring guarded by mbarriers. Warp roles:
+// CTA tile 128 x 256, K step 64 (one 128-byte swizzle row of 16-bit values),
+// 4-stage TMA -> shared-memory ring guarded by mbarriers. Persistent: one CTA
+// per SM walks a static list of tiles; the K axis is accumulated in 256-wide
+// chunks, alternately in two TMEM buffers, and each chunk is added into FP32
+// registers by the epilogue warps (the tensor core's own FP32 accumulation
+// truncates). Warp roles:
 //   warp 0  (one thread)  TMA producer
 //   warp 1  (one thread)  tcgen05.mma issuer; the whole warp owns the TMEM allocation
-//   warps 2-5             epilogue: tcgen05.ld of the accumulator (warp w reads
-//                         TMEM lanes 32*(w%4) .. +31), fused SP2 branch update
-//                         (EPI_SQUARE: sigma>0 ? C : 2X - C, FP32 master + bf16
-//                         hi/lo planes written for (i,j) and mirrored to (j,i),
-//                         FP64 trace partials) or a plain FP32 store (EPI_PLAIN).
+//   warps 2-9             epilogue: tcgen05.ld of each chunk (warp w reads TMEM
+//                         lanes 32*(w%4) .. +31, columns of half (w-2)/4), then the
+//                         fused SP2 branch update (EPI_SQUARE: sigma>0 ? C : 2X - C,
+//                         FP32 master and planes written for (i,j) and mirrored to
+//                         (j,i), trace / idempotency partials in FP32 per thread and
+//                         FP64 across) or a plain FP32 store (EPI_PLAIN).
 // Every mbarrier wait is bounded in time; on expiry the CTA raises the
 // state's abort flag, waits (bounded) for its own copies in flight and
 // returns after freeing its TMEM, and later CTAs exit at once.
