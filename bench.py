@@ -216,6 +216,19 @@ def cpu_oracle_sample(n: int, H32: np.ndarray, nocc: float):
     return dt, 2.0 * float(n) ** 3 / dt / 1e12
 
 
+def chi_config(args, ws: int) -> dict:
+    """The workload of the default line (both arms)."""
+    n = args.n
+    return {
+        "workload": (f"tight-binding N={n} ({n // 4} sites x 4 orbitals, density 0.1, r<6), "
+                     f"N_occ={n // 2}: forward SP2 (Eq. DM0) + adjoint chi (Eq. DM2) of the "
+                     f"x-dipole, X_n checkpointed every {args.ckpt_k} steps"),
+        "n": n, "mode": args.mode, "ckpt_k": args.ckpt_k, "global_batch": ws,
+        "parallelism": f"replicas x{ws}",
+        "l2": "inputs larger than L2 (each N x N FP32 matrix is 1 GiB at N=16384)",
+    }
+
+
 def run_reference(args, ws, rank):
     """The oracle as it stands on the host cores, on this workload: each step
     is one FP64 SP2 step (one N x N x N product) at N = args.n."""
@@ -235,8 +248,7 @@ def run_reference(args, ws, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"tight-binding N={args.n}, FP64 oracle, one SP2 step (one N^3 product) per step",
-                   "n": args.n},
+        "config": chi_config(args, ws),
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"one FP64 SP2 step at N={args.n} per step (numpy/BLAS, all host threads)"},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -306,14 +318,7 @@ def run_ours(args, ws, rank):
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"{args.mode} (split 16-bit products, f32 accumulate/master)",
         "data": "synthetic",
-        "config": {
-            "workload": (f"tight-binding N={n} ({n // 4} sites x 4 orbitals, density 0.1, r<6), "
-                         f"N_occ={tb.nocc}: forward SP2 (Eq. DM0) + adjoint chi (Eq. DM2) of the "
-                         f"x-dipole, X_n checkpointed every {args.ckpt_k} steps"),
-            "n": n, "mode": args.mode, "ckpt_k": args.ckpt_k, "global_batch": ws,
-            "parallelism": f"replicas x{ws}",
-            "l2": "inputs larger than L2 (each N x N FP32 matrix is 1 GiB)",
-        },
+        "config": chi_config(args, ws),
         "ms_per_solve": ms_max, "tflops_effective": value / ws, "tflops_executed": exec_tflops,
         "tc_peak_frac_executed": exec_tflops / peak,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
