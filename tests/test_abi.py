@@ -110,3 +110,23 @@ def test_null_handle_is_rejected(lib):
     assert lib.sp2_destroy(None) == _lib.EINVAL
     assert lib.sp2_density(None, None, 4, 0, 2.0, None, None, None) == _lib.EINVAL
     assert lib.sp2_create(None, None, 0) == _lib.EINVAL
+
+
+def test_make_opts_host_only(lib):
+    """The binding's option marshalling is host code: the automatic checkpoint
+    interval, the mode names (BF16X3 included) and the branch array."""
+    from paper_2409_17033_gb300 import _lib, api
+    o, keep = api.make_opts("bf16x3", ckpt_k="auto", sigma=[1, -1, 1])
+    assert o.mode == _lib.MODE_BF16X3 == 4
+    assert o.ckpt_k == _lib.CKPT_AUTO == -1
+    assert o.fixed_m == 3 and [o.sigma_in[i] for i in range(3)] == [1, -1, 1]
+    o2, _ = api.make_opts("fp16x2", ckpt_k=1, bounds=(-2.0, 3.0))
+    assert o2.ckpt_k == 1 and (o2.eps_min, o2.eps_max) == (-2.0, 3.0)
+
+
+def test_info_dict_fields(lib):
+    """sp2_info exposes the checkpoint interval used and the refinement /
+    Newton-Schulz iteration field to Python."""
+    from paper_2409_17033_gb300 import _lib
+    d = _lib.Info().to_dict()
+    assert "ckpt_k" in d and "refine_iter" in d
