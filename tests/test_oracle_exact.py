@@ -200,3 +200,17 @@ def test_three_plane_product_accuracy():
     e2 = np.max(np.abs(split.mixed_product(X, Y, "bf16") - exact_) / scale)
     assert e3 < 4 * 2.0 ** -24
     assert e2 > 16 * e3
+
+
+def test_three_plane_pin_catches_a_dropped_term():
+    """Dropping one of the 2^-16 terms (mid.mid) from the six-term product
+    moves it far outside the 4 * 2^-24 bound of the accuracy pin."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((64, 64)).astype(np.float32)
+    Y = rng.standard_normal((64, 64)).astype(np.float32)
+    exact_ = X.astype(np.float64) @ Y.astype(np.float64)
+    scale = np.abs(X).astype(np.float64) @ np.abs(Y).astype(np.float64)
+    xh, xm, xl = (a.astype(np.float64) for a in split.split_hi_mid_lo(X))
+    yh, ym, yl = (a.astype(np.float64) for a in split.split_hi_mid_lo(Y))
+    wrong = xh @ yh + (xh @ ym + xm @ yh) + (xh @ yl + xl @ yh)
+    assert np.max(np.abs(wrong - exact_) / scale) > 4 * 2.0 ** -24

@@ -56,3 +56,27 @@ def test_orthonormal_limit(prob):
     e, V = exact.eigh(prob.H)
     assert np.allclose(WH, exact.response_zero_T(e, V, prob.nocc, prob.A), atol=1e-12)
     assert np.allclose(D, exact.density_zero_T(e, V, prob.nocc), atol=1e-12)
+
+
+@pytest.mark.parametrize("mistake", ["ws_sign", "ws_drop_ad", "wh_transpose_z"])
+def test_planted_mistakes_fail_the_pin(prob, mistake):
+    """A plausible slip in the weights (a flipped sign, a dropped term, Z on the
+    wrong side) breaks agreement with the finite differences of the generalized
+    eigenproblem, so the pin above would catch it."""
+    Z, D, WH, WS = nonorth.dual_weights(prob.H, prob.S, prob.A, prob.nocc)
+    Sinv = Z @ Z.T
+    if mistake == "ws_sign":
+        WS = -WS
+    elif mistake == "ws_drop_ad":
+        P = Sinv @ prob.A @ D
+        WS = WS + 0.5 * (P + P.T)
+    else:
+        WH = Z.T @ WH @ Z     # chi moved through the congruence twice
+    At, Ht, St = prob.A_t[0], prob.H_t[0], prob.S_t[0]
+    h = 1e-5
+
+    def a(t):
+        Dt = nonorth.density_generalized(prob.H + t * Ht, prob.S + t * St, prob.nocc)
+        return float(np.sum((prob.A + t * At) * Dt))
+    fd = (a(h) - a(-h)) / (2 * h)
+    assert nonorth.derivative_dual(D, WH, WS, At, Ht, St) != pytest.approx(fd, rel=1e-4)
