@@ -173,6 +173,31 @@ const char* sp2_last_error(sp2_handle_t h);
 /* Bytes of device memory the handle currently holds. */
 size_t sp2_workspace_bytes(sp2_handle_t h);
 
+/* Launch settings of the tensor-core product kernel (not part of the arithmetic).
+ *   SP2_OPTION_WAIT_LIMIT_NS  limit of every bounded device wait, in ns (default
+ *                             2e9). When a wait runs out the kernel raises an abort
+ *                             flag, drains its own copies and tensor-core work,
+ *                             frees its tensor memory and returns; the call then
+ *                             returns SP2_ETIMEOUT and the handle stays usable.
+ *   SP2_OPTION_WITHHOLD_LOAD  test hook for that path: != 0 makes the first
+ *                             operand load of the first CTA of every product
+ *                             launch never be issued, so the wait for it runs out
+ *                             (use with a short wait limit). Default 0.
+ *   SP2_OPTION_FUSED_RESPONSE != 0: each response step of the split modes is one
+ *                             tensor-core launch over the upper tiles that forms
+ *                             Y X + X Y as [Y | X] . [X ; Y] and applies the branch
+ *                             update in its epilogue (no Y X buffer, no separate
+ *                             transpose-add pass); 0 (default): Y X, then the
+ *                             transpose-add kernel. Same arithmetic up to rounding
+ *                             order.
+ * Returns SP2_EINVAL for an unknown option or a value out of range. */
+typedef enum {
+  SP2_OPTION_WAIT_LIMIT_NS = 0,
+  SP2_OPTION_WITHHOLD_LOAD = 1,
+  SP2_OPTION_FUSED_RESPONSE = 2
+} sp2_option;
+int sp2_set_option(sp2_handle_t h, int option, int64_t value);
+
 /* Eq. DM0. H: N x N input. nocc: N_occ in [0, N]. D: N x N output.
  * info (nullable, host): M, branch sequence, errors, alpha/beta. */
 int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc,
@@ -335,8 +360,9 @@ int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, i
  * loads libsp2.so holds until the process exits. The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress, with that
  * device current) and caches it; make that first call before any stream
- * capture begins. P, Q and out must be device memory (host pointers are
- * rejected); out[l*K + k] = sum_ij P_l[i,j] Q_k[i,j] as in response_contract.
+ * capture begins. P, Q and out must be device memory of the current device
+ * (host pointers and memory of another GPU are rejected);
+ * out[l*K + k] = sum_ij P_l[i,j] Q_k[i,j] as in response_contract.
  * The work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy
  * default stream) and the call returns without waiting: out is valid once
  * the stream has reached it. All calls share the one partial-sum array,
@@ -344,8 +370,8 @@ int response_contract(sp2_handle_t h, const void* P, int64_t L, const void* Q, i
  * by that same call first, so nothing needs clearing, but calls whose work
  * overlaps on the GPU (other streams, other host threads) race on the array
  * and must be ordered by the caller.
- * Returns SP2_EINVAL for negative sizes, a bad dtype, null or host pointers,
- * or L * K > 65535; SP2_ECUDA if a CUDA call fails. */
+ * Returns SP2_EINVAL for negative sizes, a bad dtype, null, host or
+ * other-GPU pointers, or L * K > 65535; SP2_ECUDA if a CUDA call fails. */
 int response_contract_noalloc(const void* P, int64_t L, const void* Q, int64_t K, int64_t N,
                               int dtype, int q_diag_only, double* out, void* cuda_stream);
 

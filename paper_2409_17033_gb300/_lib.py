@@ -27,6 +27,8 @@ MODE_FP64, MODE_FP32, MODE_BF16X2, MODE_FP16X2, MODE_BF16X3 = 0, 1, 2, 3, 4
 MODES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16x2": MODE_BF16X2, "fp16x2": MODE_FP16X2,
          "bf16x3": MODE_BF16X3}
 CKPT_AUTO = -1   # SP2_CKPT_AUTO
+# sp2_option
+OPTION_WAIT_LIMIT_NS, OPTION_WITHHOLD_LOAD, OPTION_FUSED_RESPONSE = 0, 1, 2
 
 
 class Opts(C.Structure):
@@ -122,6 +124,7 @@ EXPORTS = {
     "sp2_destroy": (C.c_int, [C.c_void_p]),
     "sp2_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sp2_last_error": (C.c_char_p, [C.c_void_p]),
+    "sp2_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "sp2_workspace_bytes": (C.c_size_t, [C.c_void_p]),
     "sp2_density": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double,
                               C.POINTER(Opts), C.c_void_p, C.POINTER(Info)]),

@@ -113,6 +113,13 @@ class Handle:
             return
         raise L.SP2Error(rc, self.lib.sp2_last_error(self.h).decode())
 
+    def set_option(self, option: str, value: int):
+        """Product-kernel launch settings (sp2_set_option): "wait_limit_ns",
+        "withhold_load" (test hook of the timed-out wait path) or "fused_response"."""
+        code = {"wait_limit_ns": L.OPTION_WAIT_LIMIT_NS, "withhold_load": L.OPTION_WITHHOLD_LOAD,
+                "fused_response": L.OPTION_FUSED_RESPONSE}[option]
+        self.check(self.lib.sp2_set_option(self.h, code, int(value)))
+
     def workspace_bytes(self) -> int:
         return int(self.lib.sp2_workspace_bytes(self.h))
 

@@ -39,13 +39,16 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of the current device: memory of another GPU may
+// not be reachable from this one, and a kernel touching it would fault.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -58,7 +61,13 @@ extern "C" int response_contract_noalloc(const void* P, int64_t L, const void* Q
   if (L == 0 || K == 0) return SP2_OK;
   if (L * K > kMaxPairs) return SP2_EINVAL;  // more (l, k) pairs than the scratch serves
   if (!out || (N > 0 && (!P || !Q))) return SP2_EINVAL;
-  if (!on_device(out) || (N > 0 && (!on_device(P) || !on_device(Q)))) return SP2_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SP2_ECUDA;
+  }
+  if (!on_device(out, dev) || (N > 0 && (!on_device(P, dev) || !on_device(Q, dev))))
+    return SP2_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (N == 0)
     return cudaMemsetAsync(out, 0, sizeof(double) * L * K, s) == cudaSuccess ? SP2_OK : SP2_ECUDA;

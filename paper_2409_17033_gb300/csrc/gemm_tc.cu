@@ -1,38 +1,52 @@
 // Split-precision tensor-core product kernel for sm_103a (tcgen05 + TMEM + TMA).
 //
-// Computes C = A X for the SP2 path with the hi/lo splitting of Eq. doubleHalf
-// and the three-product form of Eq. MixPrecMult / Eq. mults (lo*lo dropped):
-//     A X ~ A_hi X_hi + A_hi X_lo + A_lo X_hi,
-// evaluated over a concatenated K axis of length 3 np,
-//     [A_hi | A_hi | A_lo] . [X_hi ; X_lo ; X_hi],
-// into FP32 accumulators in tensor memory. X is symmetric, so the row-major
-// X planes are directly the K-major B operand.
-//   BF16X2: one accumulator for all three segments.
+// Computes the products of the SP2 path with the hi/lo splitting of Eq.
+// doubleHalf and the three-product form of Eq. MixPrecMult / Eq. mults (lo*lo
+// dropped):
+//     P Q ~ P_hi Q_hi + P_hi Q_lo + P_lo Q_hi,
+// evaluated over a concatenated K axis, [P_hi | P_hi | P_lo] . [Q_hi ; Q_lo ; Q_hi],
+// into FP32 accumulators in tensor memory. Every right factor Q is symmetric,
+// so its row-major planes are directly the K-major B operand.
+//   BF16X2: bfloat16 planes, one weight for all segments.
 //   BF16X3: three bfloat16 planes (hi + mid + lo = the FP32 value) and six
-//           segments [A_h|A_h|A_m|A_h|A_m|A_l] . [X_h;X_m;X_h;X_l;X_m;X_h]: every
-//           term down to 2^-16 relative, K = 6 np, no scaling.
-//   FP16X2: the lo planes hold residuals times 2^11, so segment 0 (hi*hi) and
-//           segments 1-2 (hi*lo, lo*hi) go to two accumulators (512 TMEM
-//           columns) combined as acc0 + 2^-11 acc1; A may carry a per-matrix
-//           power-of-two scale that the epilogue divides out.
+//           segments [P_h|P_h|P_m|P_h|P_m|P_l] . [Q_h;Q_m;Q_h;Q_l;Q_m;Q_h]: every
+//           term down to 2^-16 relative, no scaling.
+//   FP16X2: the lo planes hold residuals times 2^11; chunks of the hi*lo and
+//           lo*hi segments are weighted by 2^-11 when they are drained from
+//           TMEM. P may carry a per-matrix power-of-two scale that the epilogue
+//           divides out.
+// Epilogues:
+//   EPI_SQUARE  X_{n+1} = sigma_n > 0 ? X_n^2 : 2 X_n - X_n^2 (Eq. DM0), upper
+//               tiles only, mirrored; partials of Tr X_{n+1}, ||X_{n+1}||_F^2 and
+//               ||X_n - X_n^2||_F^2 for the branch and stop decisions.
+//   EPI_PLAIN   C = P Q stored as it is (FP32).
+//   EPI_SYMM    Y_{n+1} = sigma_n > 0 ? Y_n X_n + X_n Y_n : 2 Y_n - (Y_n X_n + X_n Y_n)
+//               (Eqs. DM1, DM2, DM3) for a stacked batch of symmetric Y. With X
+//               and Y symmetric, (X Y)(I, J) = X(I, :) Y(:, J), so each upper tile
+//               of Y X + X Y is ONE accumulation over the doubled K axis
+//               [P | Q] . [Q ; P] (P = Y, Q = X): no Z buffer and no transpose
+//               pass. Partials of ||Y_{n+1}||_F^2 per tile (FP16X2 plane scales).
 //
 // CTA tile 128 x 256, K step 64 (one 128-byte swizzle row of 16-bit values),
-// 4-stage TMA -> shared-memory ring guarded by mbarriers. Persistent: one CTA
-// per SM walks a static list of tiles; the K axis is accumulated in 256-wide
-// chunks, alternately in two TMEM buffers, and each chunk is added into FP32
-// registers by the epilogue warps (the tensor core's own FP32 accumulation
-// truncates). Warp roles:
+// 4-stage TMA -> shared-memory
+// ring guarded by mbarriers. Persistent: one CTA per SM walks tiles b, b+G,
+// b+2G, ... of a static list. The K axis is accumulated in 256-wide chunks,
+// alternately in two TMEM buffers, and each chunk is added into FP32 registers
+// by the epilogue warps (the tensor core's own FP32 accumulation truncates).
+//
+// Warp roles:
 //   warp 0  (one thread)  TMA producer
 //   warp 1  (one thread)  tcgen05.mma issuer; the whole warp owns the TMEM allocation
-//   warps 2-9             epilogue: tcgen05.ld of each chunk (warp w reads TMEM
-//                         lanes 32*(w%4) .. +31, columns of half (w-2)/4), then the
-//                         fused SP2 branch update (EPI_SQUARE: sigma>0 ? C : 2X - C,
-//                         FP32 master and planes written for (i,j) and mirrored to
-//                         (j,i), trace / idempotency partials in FP32 per thread and
-//                         FP64 across) or a plain FP32 store (EPI_PLAIN).
-// Every mbarrier wait is bounded in time; on expiry the CTA raises the
-// state's abort flag, waits (bounded) for its own copies in flight and
-// returns after freeing its TMEM, and later CTAs exit at once.
+//   warps 2-17            epilogue: tcgen05.ld of each chunk (warp w reads TMEM lanes
+//                         32*(w%4) .. +31, the 64 columns of group (w-2)/4), then
+//                         the epilogue above. With 64 columns per thread the chunk
+//                         drain (the tensor pipe's critical path: the MMA warp runs
+//                         at most one chunk ahead) and the tile-end stores are spread
+//                         over twice as many warps as with 128.
+// Every mbarrier wait is bounded in time (a launch parameter, default 2 s); on
+// expiry the CTA raises the state's abort flag, waits (bounded) for its own
+// copies and tensor-core operations in flight, frees its TMEM and returns, and
+// later CTAs exit at once.
 #include <cuda.h>
 
 #include <stdio.h>
@@ -51,13 +65,15 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_WARPS = 8;                     // two warps per TMEM lane quarter
-constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
+constexpr int EPI_WARPS = 16;                    // four warps per TMEM lane quarter
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int NUM_THREADS = 64 + EPI_THREADS;    // TMA warp, MMA warp, epilogue warps
 constexpr uint32_t ACC_COLS = 256;               // one 128 x 256 FP32 accumulator
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;     // two chunk buffers
-constexpr int HALF_COLS = BN / 2;                // columns per epilogue thread
+constexpr int COL_GROUPS = EPI_WARPS / 4;        // column groups of a tile
+constexpr int TCOLS = BN / COL_GROUPS;            // columns per epilogue thread
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
-constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
+constexpr unsigned long long DRAIN_NS = 200000000ull;
 
 // Instruction descriptor, kind::f16: D=F32 (bits 4-5 = 1), A and B format at
 // bits 7-9 / 10-12 (BF16 = 1, F16 = 0; always the same for A and B), both
@@ -104,14 +120,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase of parity `parity` to complete. Gives up (returning
-// false) when the abort flag is raised or after TIMEOUT_NS, raising the flag.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag) {
+// false) when the abort flag is raised or after limit_ns, raising the flag.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag,
+                          unsigned long long limit_ns) {
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*((volatile int*)abort_flag)) return false;
-      if (globaltimer() - t0 > TIMEOUT_NS) {
+      if (globaltimer() - t0 > limit_ns) {
         atomicExch(abort_flag, 1);
         return false;
       }
@@ -119,7 +136,7 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag) {
   }
 }
 
-// Same, ignoring the abort flag (drain of copies in flight), with its own limit.
+// Same, ignoring the abort flag (drain of work in flight), with its own limit.
 __device__ void mbar_wait_drain(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
   const unsigned long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity))
@@ -155,8 +172,8 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
@@ -182,15 +199,61 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 256-bit global accesses (sm_100 and later; 32-byte aligned addresses): one lane
+// moves a full 32-byte sector, where 128-bit accesses by lanes on different rows
+// would each fill half a sector.
+__device__ __forceinline__ void st256(void* p, const uint32_t (&v)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
+__device__ __forceinline__ void st256f(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+
+__device__ __forceinline__ void ld256f(const float* p, float* v) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(p)
+               : "memory");
+}
+
 // plane kinds of the product kernel
 constexpr int KIND_BF16X2 = 0, KIND_FP16X2 = 1, KIND_BF16X3 = 2;
+// plane indices of an operand: 0 = hi, 1 = lo, 2 = mid (BF16X3)
+constexpr int PL_HI = 0, PL_LO = 1, PL_MID = 2;
+
+// planes of the left and right factor in base segment `seg` (K-concatenated
+// split product), and the weight of that segment's chunks
+template <int KIND>
+__device__ __forceinline__ void seg_planes(int seg, int& pa, int& pb) {
+  if constexpr (KIND == KIND_BF16X3) {
+    // hh, hm, mh, hl, mm, lh
+    pa = (seg == 2 || seg == 4) ? PL_MID : (seg == 5 ? PL_LO : PL_HI);
+    pb = (seg == 1 || seg == 4) ? PL_MID : (seg == 3 ? PL_LO : PL_HI);
+  } else {
+    // hh, hl, lh
+    pa = seg == 2 ? PL_LO : PL_HI;
+    pb = seg == 1 ? PL_LO : PL_HI;
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ float seg_weight(int seg) {
+  if constexpr (KIND == KIND_FP16X2) return seg == 0 ? 1.0f : 1.0f / kLoScale;
+  return 1.0f;
+}
 
 template <int KIND>
 __device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* mid, uint16_t* lo, int64_t idx,
-                                            float v) {
+                                            float v, float scale) {
   uint16_t h, l;
   if constexpr (KIND == KIND_FP16X2) {
-    split_fp16(v, 1.0f, h, l);
+    split_fp16(v, scale, h, l);
   } else if constexpr (KIND == KIND_BF16X3) {
     uint16_t m;
     split_bf16x3(v, h, m, l);
@@ -204,30 +267,207 @@ __device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* mid, uint16_
 
 template <int KIND>
 __device__ __forceinline__ void store_split(float* m, uint16_t* hi, uint16_t* mid, uint16_t* lo,
-                                            int64_t idx, float v) {
+                                            int64_t idx, float v, float scale) {
   m[idx] = v;
-  split_store<KIND>(hi, mid, lo, idx, v);
+  split_store<KIND>(hi, mid, lo, idx, v, scale);
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
-          const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-          const __grid_constant__ CUtensorMap mA_mid, const __grid_constant__ CUtensorMap mB_mid,
-          int nkb, int ch, int epi, int64_t np, float* __restrict__ out,
-          uint16_t* __restrict__ out_hi, uint16_t* __restrict__ out_lo,
-          uint16_t* __restrict__ out_mid,
-          const float* __restrict__ xprev, Part3* __restrict__ part,
-          const Tile* __restrict__ tiles, int ntiles, DevState* st, int step,
-          const float* __restrict__ a_scale, const float* __restrict__ b_scale,
-          float* __restrict__ zmax) {
+struct KParams {
+  int nkb;                 // k-blocks (of BK) per segment: np / BK
+  int ch;                  // k-blocks per TMEM chunk
+  int nbase;               // segments of one split product (3, or 6 for BF16X3)
+  int nseg;                // segments on the K axis (nbase, or 2 nbase for EPI_SYMM)
+  int64_t np;
+  float* out;
+  uint16_t* out_hi;
+  uint16_t* out_lo;
+  uint16_t* out_mid;
+  const float* prev;       // EPI_SQUARE: X_n; EPI_SYMM: Y_n (stacked like out)
+  Part3* part;             // per-tile partials
+  const Tile* tiles;
+  int ntiles;
+  DevState* st;
+  int step;
+  const float* p_scale;    // FP16X2: per batch entry of P, the plane scale to divide out
+  const float* q_scale;    // FP16X2: the plane scale of Q (nullable)
+  const float* o_scale;    // FP16X2 EPI_SYMM: per batch entry, scale of the output planes
+  float* zmax;             // FP16X2 EPI_PLAIN: per batch entry, receives max |C|
+  unsigned long long wait_ns;
+  int withhold;            // test hook: CTA 0 never issues its first load
+};
+
+// Tensor maps of one launch: the left factor's planes with 128-row boxes (A role)
+// and the right factor's with 256-row boxes (B role); EPI_SYMM also reads X in
+// the A role and Y in the B role (its second half, [X | .] . [. ; Y]).
+struct KMaps {
+  CUtensorMap pa[3];   // P planes (hi, lo, mid), A role
+  CUtensorMap qb[3];   // Q planes, B role
+  CUtensorMap qa[3];   // Q planes, A role (EPI_SYMM)
+  CUtensorMap pb[3];   // P planes, B role (EPI_SYMM)
+};
+
+// The stores and partials of one finished tile: row r of the tile, columns
+// [grp * 64, grp * 64 + 64); acc holds this thread's FP32 sums. The epilogue
+// is a template parameter, so that each kernel carries only its own code (a
+// smaller kernel keeps the producer's and the MMA issuer's loops in the
+// instruction cache).
+template <int KIND, int EPI>
+__device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], int tix, int it,
+                                         int e, int lane, int grp, int r, int sg,
+                                         double (*red)[3][EPI_WARPS]) {
   constexpr bool F16 = KIND == KIND_FP16X2;
   constexpr bool X3 = KIND == KIND_BF16X3;
-  constexpr int NSEG = X3 ? 6 : 3;
+  const int64_t np = p.np;
+  const Tile t = p.tiles[tix];
+  const int64_t bat = EPI == EPI_SQUARE ? 0 : t.row0 / np;   // batch entry (stacked P)
+  const int64_t gi = t.row0 + r;                               // stacked row
+  const int64_t li = gi - bat * np;                            // row within its matrix
+  float inv_s = 1.0f;
+  if constexpr (F16) {
+    if (p.p_scale) inv_s = 1.0f / p.p_scale[bat];
+    if (p.q_scale) inv_s /= p.q_scale[0];
+  }
+  if constexpr (EPI == EPI_PLAIN) {
+    float zm = 0.0f;
+#pragma unroll
+    for (int c0 = 0; c0 < TCOLS; c0 += 16) {
+      float* dst = p.out + gi * np + t.col0 + grp * TCOLS + c0;
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        v[j] = acc[c0 + j] * inv_s;
+        zm = fmaxf(zm, fabsf(v[j]));
+      }
+      st256f(dst, v);
+      st256f(dst + 8, v + 8);
+    }
+    if (p.zmax) {
+      for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+      if (lane == 0 && zm > 0.0f) atomicMax(reinterpret_cast<int*>(&p.zmax[bat]), __float_as_int(zm));
+    }
+  } else {
+    // X_{n+1} (EPI_SQUARE: C = X_n^2) or Y_{n+1} (EPI_SYMM: C = Y_n X_n + X_n Y_n) is
+    // C for sigma > 0 and 2 M_n - C for sigma < 0 (M_n the previous iterate)
+    const float os = (F16 && EPI == EPI_SYMM && p.o_scale) ? p.o_scale[bat] : 1.0f;
+    const int64_t mbase = bat * np * np;   // first entry of this batch entry's matrix
+    // per-thread partials over at most 128 entries of one row in FP32 (GB300's FP64
+    // rate is a small fraction of its FP32 rate); lanes, warps and tiles add in FP64:
+    // Tr, ||.||_F^2 and (EPI_SQUARE) ||X_n - X_n^2||_F^2, whose residual is
+    // X_n - X_{n+1} up to its sign in either branch
+    float t1 = 0.0f, t2 = 0.0f, f = 0.0f;
+#pragma unroll
+    for (int c0 = 0; c0 < TCOLS; c0 += 16) {
+      const int64_t gj0 = t.col0 + grp * TCOLS + c0;
+      if (gj0 + 15 < li) continue;  // whole group below the diagonal
+      float val[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) val[j] = acc[c0 + j] * inv_s;
+      {
+        float xin[16];
+        if (EPI == EPI_SQUARE || sg < 0) {
+          const float* xp = p.prev + gi * np + gj0;
+          ld256f(xp, xin);
+          ld256f(xp + 8, xin + 8);
+          if (sg < 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) val[j] = 2.0f * xin[j] - val[j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t gj = gj0 + j;
+          if (gj < li) continue;
+          const float d = val[j], w2 = gj == li ? 1.0f : 2.0f;
+          if (gj == li) t1 += d;
+          t2 = fmaf(w2 * d, d, t2);
+          if constexpr (EPI == EPI_SQUARE) f = fmaf(w2 * (xin[j] - d), xin[j] - d, f);
+        }
+      }
+      uint32_t wh[8], wl[8], wm[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint16_t h0, h1, l0, l1, m0 = 0, m1 = 0;
+        if constexpr (X3) {
+          split_bf16x3(val[2 * j], h0, m0, l0);
+          split_bf16x3(val[2 * j + 1], h1, m1, l1);
+        } else if constexpr (F16) {
+          split_fp16(val[2 * j], os, h0, l0);
+          split_fp16(val[2 * j + 1], os, h1, l1);
+        } else {
+          split_bf16(val[2 * j], h0, l0);
+          split_bf16(val[2 * j + 1], h1, l1);
+        }
+        wh[j] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        wl[j] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+        wm[j] = (uint32_t)m0 | ((uint32_t)m1 << 16);
+      }
+      if (gj0 >= li) {
+        const int64_t o = gi * np + gj0;
+        st256f(p.out + o, val);
+        st256f(p.out + o + 8, val + 8);
+        st256(p.out_hi + o, wh);
+        st256(p.out_lo + o, wl);
+        if constexpr (X3) st256(p.out_mid + o, wm);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (gj0 + j >= li) {
+            const int64_t o = gi * np + gj0 + j;
+            const int sh = 16 * (j & 1);
+            p.out[o] = val[j];
+            p.out_hi[o] = (uint16_t)(wh[j >> 1] >> sh);
+            p.out_lo[o] = (uint16_t)(wl[j >> 1] >> sh);
+            if constexpr (X3) p.out_mid[o] = (uint16_t)(wm[j >> 1] >> sh);
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int64_t gj = gj0 + j;
+        if (gj <= li) continue;
+        const int64_t o = mbase + gj * np + li;
+        const int sh = 16 * (j & 1);
+        p.out[o] = val[j];
+        p.out_hi[o] = (uint16_t)(wh[j >> 1] >> sh);
+        p.out_lo[o] = (uint16_t)(wl[j >> 1] >> sh);
+        if constexpr (X3) p.out_mid[o] = (uint16_t)(wm[j >> 1] >> sh);
+      }
+    }
+    double d1 = t1, d2 = t2, d3 = f;
+    for (int o = 16; o > 0; o >>= 1) {
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+    }
+    const int pb = it & 1;
+    if (lane == 0) {
+      red[pb][0][e] = d1;
+      red[pb][1][e] = d2;
+      red[pb][2][e] = d3;
+    }
+    // epilogue warps only (named barrier 1): one thread writes the tile's partials
+    asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS) : "memory");
+    if (e == 0 && lane == 0) {
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int w = 0; w < EPI_WARPS; ++w) {
+        s1 += red[pb][0][w];
+        s2 += red[pb][1][w];
+        s3 += red[pb][2][w];
+      }
+      p.part[tix] = Part3{s1, s2, s3};
+    }
+  }
+}
+
+template <int KIND, int EPI>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
+  constexpr bool F16 = KIND == KIND_FP16X2;
+  constexpr bool X3 = KIND == KIND_BF16X3;
   constexpr uint32_t kIdesc = idesc_for(F16);
+  DevState* st = p.st;
   {
     const int m = *((volatile const int*)&st->stop_at);
-    if ((m != 0 && step > m) || *((volatile const int*)&st->abort_flag)) return;
+    if ((m != 0 && p.step > m) || *((volatile const int*)&st->abort_flag)) return;
   }
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -236,15 +476,17 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;   // [2] chunk accumulated in TMEM buffer b
   uint64_t* tempty = tfull + 2;       // [2] TMEM buffer b drained by the epilogue warps
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* mdone = tempty + 2;       // abort path: the MMA issuer's last operations done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   __shared__ double red[2][3][EPI_WARPS];   // per-tile partials, double-buffered by tile parity
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* abortf = &st->abort_flag;
-  const int total_kb = NSEG * nkb;
-  const int nchunks = total_kb / ch;
+  const int total_kb = p.nseg * p.nkb;
+  const int nchunks = total_kb / p.ch;
   // persistent static schedule: this CTA handles tiles blockIdx.x, +gridDim.x, ...
-  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int my_tiles =
+      (int)blockIdx.x < p.ntiles ? (p.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -255,9 +497,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], EPI_WARPS);
     }
+    mbar_init(mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA_hi)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB_hi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.pa[0])) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.qb[0])) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -273,64 +516,65 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
 
   if (warp == 0) {
     if (lane == 0) {
+      const int64_t np = p.np;
+      const int nkb = p.nkb;
       // k-block counter g runs on across tiles: stage g % STAGES, phase (g / STAGES) & 1
-      int64_t issued = 0;
+      int64_t g = 0;
       bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it) {
-        const Tile t = tiles[blockIdx.x + (int64_t)it * gridDim.x];
-        for (int kb = 0; kb < total_kb; ++kb) {
-          const int64_t g = (int64_t)it * total_kb + kb;
+        const Tile t = p.tiles[blockIdx.x + it * gridDim.x];
+        const int bat = (int)(t.row0 / np);
+        for (int kb = 0; kb < total_kb; ++kb, ++g) {
           const int s = (int)(g % STAGES);
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, abortf)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
             ok = false;
             break;
           }
+          if (p.withhold && blockIdx.x == 0 && g == 0) continue;  // test hook: never completes
           const int seg = kb / nkb;
           const int kx = (kb - seg * nkb) * BK;
-          const CUtensorMap* ma;
-          const CUtensorMap* mb;
-          if constexpr (X3) {
-            // segments hh, hm, mh, hl, mm, lh
-            ma = (seg == 2 || seg == 4) ? &mA_mid : (seg == 5 ? &mA_lo : &mA_hi);
-            mb = (seg == 1 || seg == 4) ? &mB_mid : (seg == 3 ? &mB_lo : &mB_hi);
-          } else {
-            ma = seg < 2 ? &mA_hi : &mA_lo;
-            mb = seg == 1 ? &mB_lo : &mB_hi;
-          }
+          const bool swap = EPI == EPI_SYMM && seg >= p.nbase;   // second half: [Q | .] . [. ; P]
+          int pa, pb;
+          seg_planes<KIND>(swap ? seg - p.nbase : seg, pa, pb);
+          const CUtensorMap* ma = swap ? &maps.qa[pa] : &maps.pa[pa];
+          const CUtensorMap* mb = swap ? &maps.pb[pb] : &maps.qb[pb];
+          const int arow = swap ? t.row0 - bat * (int)np : t.row0;
+          const int brow = swap ? bat * (int)np + t.col0 : t.col0;
           uint8_t* sa = smem + s * STAGE_BYTES;
           mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-          tma_load_2d(ma, &full[s], sa, kx, t.row0);
-          tma_load_2d(mb, &full[s], sa + A_BYTES, kx, t.col0);
-          issued = g + 1;
+          tma_load_2d(ma, &full[s], sa, kx, arow);
+          tma_load_2d(mb, &full[s], sa + A_BYTES, kx, brow);
         }
       }
       if (!ok) {
         // aborted: let the copies already issued land before the CTA exits
-        const int64_t first = issued > STAGES ? issued - STAGES : 0;
-        for (int64_t g = first; g < issued; ++g)
-          mbar_wait_drain(&full[g % STAGES], (uint32_t)(g / STAGES) & 1u, 200000000ull);
+        const int64_t first = g > STAGES ? g - STAGES : 0;
+        for (int64_t q = first; q < g; ++q) {
+          if (p.withhold && blockIdx.x == 0 && q == 0) continue;
+          mbar_wait_drain(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, DRAIN_NS);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      const int ch = p.ch;
       bool ok = true;
+      int64_t g = 0, gc = 0;   // k-block and chunk counters across tiles
       for (int it = 0; it < my_tiles && ok; ++it) {
-        for (int c = 0; c < nchunks && ok; ++c) {
-          const int64_t gc = (int64_t)it * nchunks + c;  // chunk counter across tiles
+        for (int c = 0; c < nchunks && ok; ++c, ++gc) {
           const int b = (int)(gc & 1);
           // the epilogue has drained buffer b (chunk gc-2)
-          if (!mbar_wait(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf)) {
+          if (!mbar_wait(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf, p.wait_ns)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
-          for (int kb = c * ch; kb < (c + 1) * ch; ++kb) {
-            const int64_t g = (int64_t)it * total_kb + kb;
+          for (int kb = c * ch; kb < (c + 1) * ch; ++kb, ++g) {
             const int s = (int)(g % STAGES);
             const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, abortf)) {
+            if (!mbar_wait(&full[s], ph, abortf, p.wait_ns)) {
               ok = false;
               break;
             }
@@ -341,56 +585,68 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
               // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
-              umma_bf16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
-                        (kb > c * ch || k > 0) ? 1u : 0u);
+              umma_f16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                       (kb > c * ch || k > 0) ? 1u : 0u);
             }
             umma_commit(&empty[s]);
           }
-          umma_commit(&tfull[b]);
+          if (ok) umma_commit(&tfull[b]);
         }
+      }
+      if (!ok) {
+        // aborted: the tensor-core operations already issued still read the ring and
+        // write TMEM; one more commit tracks all of them (bounded wait) before dealloc
+        umma_commit(mdone);
+        mbar_wait_drain(mdone, 0, DRAIN_NS);
       }
     }
   } else {
     // epilogue warps 2 .. 2+EPI_WARPS-1: warp w reads TMEM lanes 32*(w%4) .. +31 and
-    // columns [half*128, half*128+128). Each K chunk is drained from TMEM into
-    // FP32 registers with round-to-nearest adds (FP16X2: chunks of the hi*lo
-    // segments weighted by 2^-11); the tile's stores follow while the MMA warp
-    // already fills the freed TMEM buffers with the next tile's chunks.
+    // columns [grp*64, grp*64+64). Each K chunk is drained from TMEM into
+    // FP32 registers with round-to-nearest adds; the tile's stores follow while
+    // the MMA warp already fills the freed TMEM buffers with the next tile's chunks.
+    // The drain loop is the tensor pipe's critical path (the MMA warp runs at most
+    // one chunk ahead), so it keeps nothing live beyond the accumulator.
     const int e = warp - 2;
     const int q = warp & 3;
-    const int half = e >> 2;
+    const int grp = e >> 2;
     const int r = q * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HALF_COLS);
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(grp * TCOLS);
+    // the branch of this step (uniform over the launch); the previous iterate is
+    // read by the square and, for sigma < 0, by the response update
+    const int sg = EPI == EPI_PLAIN ? 1 : p.st->sigma[p.step];
+    const bool need_prev = EPI == EPI_SQUARE || (EPI == EPI_SYMM && sg < 0);
     bool ok = true;
+    int64_t gc = 0;
     for (int it = 0; it < my_tiles && ok; ++it) {
       const int tix = blockIdx.x + it * gridDim.x;
-      const Tile t = tiles[tix];
-      const int64_t gi = t.row0 + r;
-      float acc[HALF_COLS];
+      // the previous-iterate entries the tile-end epilogue reads (256 B of this
+      // thread's row), pulled into L2 two chunks ahead of the tile's end
+      const float* pf = nullptr;
+      if (need_prev) {
+        const Tile t = p.tiles[tix];
+        pf = p.prev + ((int64_t)t.row0 + r) * p.np + t.col0 + grp * TCOLS;
+      }
+      float acc[TCOLS];
 #pragma unroll
-      for (int j = 0; j < HALF_COLS; ++j) acc[j] = 0.0f;
-      for (int c = 0; c < nchunks; ++c) {
-        const int64_t gc = (int64_t)it * nchunks + c;
+      for (int j = 0; j < TCOLS; ++j) acc[j] = 0.0f;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
         const int b = (int)(gc & 1);
-        bool w = mbar_wait(&tfull[b], (uint32_t)(gc >> 1) & 1u, abortf);
+        bool w = mbar_wait(&tfull[b], (uint32_t)(gc >> 1) & 1u, abortf, p.wait_ns);
         w = __all_sync(0xffffffffu, w);
         if (!w) {
           ok = false;
           break;
         }
         tc_fence_after();
-        if (epi == EPI_SQUARE && c == nchunks - 2) {
-          // the X_n entries the tile-end epilogue reads (512 B of this thread's row):
-          // pulled into L2 two chunks ahead, while the MMA warp can run only one
-          // chunk ahead of the epilogue
-          const float* xr = xprev + gi * np + t.col0 + half * HALF_COLS;
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xr),
-                       "r"((uint32_t)(HALF_COLS * sizeof(float)))
+        if (pf && c == nchunks - 2)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf),
+                       "r"((uint32_t)(TCOLS * sizeof(float)))
                        : "memory");
-        }
-        const float wgt = (F16 && (c * ch) >= nkb) ? (1.0f / kLoScale) : 1.0f;
+        float wgt = 1.0f;
+        if constexpr (F16) wgt = (((c * p.ch) / p.nkb) % p.nbase) == 0 ? 1.0f : 1.0f / kLoScale;
 #pragma unroll
-        for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
+        for (int c0 = 0; c0 < TCOLS; c0 += 16) {
           uint32_t v[16];
           tmem_ld16(trow + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
 #pragma unroll
@@ -401,127 +657,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUt
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
       if (!ok || *((volatile int*)abortf)) break;
-      // per-thread partials over at most 128 entries of one row in FP32 (GB300's FP64
-      // rate is a small fraction of its FP32 rate); lanes, warps and tiles add in FP64
-      float t1 = 0.0f, t2 = 0.0f, f = 0.0f;
-      const int sg = (epi == EPI_SQUARE) ? st->sigma[step] : 1;
-      const int64_t bat = gi / np;  // batch entry of this row (stacked A)
-      float inv_s = (F16 && a_scale) ? 1.0f / a_scale[bat] : 1.0f;
-      if (F16 && b_scale) inv_s /= b_scale[0];
-      float zm = 0.0f;
-#pragma unroll
-      for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
-        float val[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) val[j] = acc[c0 + j] * inv_s;
-        const int64_t gj0 = t.col0 + half * HALF_COLS + c0;
-        if (epi == EPI_PLAIN) {
-          float4* dst = reinterpret_cast<float4*>(out + gi * np + gj0);
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            dst[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) zm = fmaxf(zm, fabsf(val[j]));
-          continue;
-        }
-        if (gj0 + 15 < gi) continue;  // whole chunk below the diagonal
-        float xin[16];  // X_n: the 2X - X^2 branch and the Frobenius idempotency error
-        {
-          const float4* xp = reinterpret_cast<const float4*>(xprev + gi * np + gj0);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float4 x = xp[j];
-            xin[4 * j + 0] = x.x;
-            xin[4 * j + 1] = x.y;
-            xin[4 * j + 2] = x.z;
-            xin[4 * j + 3] = x.w;
-          }
-        }
-        float res[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          res[j] = xin[j] - val[j];
-          if (sg < 0) val[j] = 2.0f * xin[j] - val[j];
-        }
-        if (gj0 >= gi) {
-          // whole chunk on or above the diagonal: vector stores
-          float4* dm = reinterpret_cast<float4*>(out + gi * np + gj0);
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            dm[j] = make_float4(val[4 * j], val[4 * j + 1], val[4 * j + 2], val[4 * j + 3]);
-          __align__(16) uint16_t hh[16], ll[16];
-          if constexpr (X3) {
-            __align__(16) uint16_t mm[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) split_bf16x3(val[j], hh[j], mm[j], ll[j]);
-            uint4* dmid = reinterpret_cast<uint4*>(out_mid + gi * np + gj0);
-            dmid[0] = reinterpret_cast<const uint4*>(mm)[0];
-            dmid[1] = reinterpret_cast<const uint4*>(mm)[1];
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (F16) split_fp16(val[j], 1.0f, hh[j], ll[j]);
-              else split_bf16(val[j], hh[j], ll[j]);
-            }
-          }
-          uint4* dh = reinterpret_cast<uint4*>(out_hi + gi * np + gj0);
-          uint4* dl = reinterpret_cast<uint4*>(out_lo + gi * np + gj0);
-          dh[0] = reinterpret_cast<const uint4*>(hh)[0];
-          dh[1] = reinterpret_cast<const uint4*>(hh)[1];
-          dl[0] = reinterpret_cast<const uint4*>(ll)[0];
-          dl[1] = reinterpret_cast<const uint4*>(ll)[1];
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (gj0 + j >= gi)
-              store_split<KIND>(out, out_hi, out_mid, out_lo, gi * np + gj0 + j, val[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int64_t gj = gj0 + j;
-          if (gj < gi) continue;
-          const float d = val[j], rr = res[j];
-          if (gj == gi) {
-            t1 += d;
-            t2 = fmaf(d, d, t2);
-            f = fmaf(rr, rr, f);
-          } else {
-            store_split<KIND>(out, out_hi, out_mid, out_lo, gj * np + gi, val[j]);  // mirror (coalesced over lanes)
-            t2 = fmaf(2.0f * d, d, t2);
-            f = fmaf(2.0f * rr, rr, f);
-          }
-        }
-      }
-      if (epi == EPI_PLAIN && zmax) {
-        for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
-        if (lane == 0 && zm > 0.0f)
-          atomicMax(reinterpret_cast<int*>(&zmax[bat]), __float_as_int(zm));
-      }
-      if (epi == EPI_SQUARE) {
-        double d1 = t1, d2 = t2, d3 = f;
-        for (int o = 16; o > 0; o >>= 1) {
-          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-          d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-          d3 += __shfl_xor_sync(0xffffffffu, d3, o);
-        }
-        const int pb = it & 1;
-        if (lane == 0) {
-          red[pb][0][e] = d1;
-          red[pb][1][e] = d2;
-          red[pb][2][e] = d3;
-        }
-        // epilogue warps only (named barrier 1): one thread writes the tile's partials
-        asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
-        if (e == 0 && lane == 0) {
-          double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-          for (int w = 0; w < EPI_WARPS; ++w) {
-            s1 += red[pb][0][w];
-            s2 += red[pb][1][w];
-            s3 += red[pb][2][w];
-          }
-          part[tix] = Part3{s1, s2, s3};
-        }
-      }
+      tile_end<KIND, EPI>(p, acc, tix, it, e, lane, grp, r, sg, red);
     }
   }
 
@@ -544,12 +680,12 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 EncodeTiledFn get_encode() {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
-    void* p = nullptr;
+    void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
   }
   return fn;
 }
@@ -569,6 +705,27 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int bo
   return r == CUDA_SUCCESS;
 }
 
+// one launch of the (KIND, EPI) kernel, with its shared-memory attribute set once
+template <int KIND, int EPI>
+cudaError_t launch_kind(const KMaps& maps, const KParams& p, int grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<KIND, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gemm_tc<KIND, EPI><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(maps, p);
+  return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_epi(int epi, const KMaps& maps, const KParams& p, int grid, cudaStream_t s) {
+  if (epi == EPI_SQUARE) return launch_kind<KIND, EPI_SQUARE>(maps, p, grid, s);
+  if (epi == EPI_SYMM) return launch_kind<KIND, EPI_SYMM>(maps, p, grid, s);
+  return launch_kind<KIND, EPI_PLAIN>(maps, p, grid, s);
+}
+
 }  // namespace
 
 void tc_tile_shape(int* bm, int* bn) {
@@ -576,61 +733,7 @@ void tc_tile_shape(int* bm, int* bn) {
   *bn = BN;
 }
 
-cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
-                           const float* x_prev, Part3* part, const Tile* tiles, int ntiles,
-                           DevState* st, int step, const float* a_scale, float* zmax,
-                           cudaStream_t s, char* errbuf, size_t errlen, const float* b_scale) {
-  if (ntiles <= 0) return cudaSuccess;
-  const int kind = mode == SP2_MODE_FP16X2 ? KIND_FP16X2
-                                           : (mode == SP2_MODE_BF16X3 ? KIND_BF16X3 : KIND_BF16X2);
-  const bool f16 = kind == KIND_FP16X2, x3 = kind == KIND_BF16X3;
-  static bool attr_done[3] = {false, false, false};
-  if (!attr_done[kind]) {
-    cudaError_t e = kind == KIND_FP16X2
-                        ? cudaFuncSetAttribute(k_gemm_tc<KIND_FP16X2>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
-                    : kind == KIND_BF16X3
-                        ? cudaFuncSetAttribute(k_gemm_tc<KIND_BF16X3>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)
-                        : cudaFuncSetAttribute(k_gemm_tc<KIND_BF16X2>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_done[kind] = true;
-  }
-  // the middle planes exist only in BF16X3; elsewhere the hi maps stand in (never read)
-  const uint16_t* a_mid = x3 ? A.mid : A.hi;
-  const uint16_t* b_mid = x3 ? B.mid : B.hi;
-  if (x3 && (!a_mid || !b_mid || (epi == EPI_SQUARE && !out.mid))) {
-    snprintf(errbuf, errlen, "tcgen05 product: BF16X3 operand without its middle plane");
-    return cudaErrorInvalidValue;
-  }
-  // TMA box/stride rules: 16-byte aligned bases, np*2-byte row pitch (np % 256 == 0),
-  // every x coordinate a multiple of 64 elements.
-  if ((reinterpret_cast<uintptr_t>(A.hi) | reinterpret_cast<uintptr_t>(A.lo) |
-       reinterpret_cast<uintptr_t>(B.hi) | reinterpret_cast<uintptr_t>(B.lo) |
-       reinterpret_cast<uintptr_t>(a_mid) | reinterpret_cast<uintptr_t>(b_mid)) & 15u ||
-      np % 256 != 0 || A.rows % BM != 0 || B.rows % BN != 0) {
-    snprintf(errbuf, errlen, "tcgen05 product: operand alignment/shape violates the TMA rules");
-    return cudaErrorInvalidValue;
-  }
-  CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid;
-  if (!make_map(&ma_hi, A.hi, A.rows, np, BM, f16) || !make_map(&ma_lo, A.lo, A.rows, np, BM, f16) ||
-      !make_map(&mb_hi, B.hi, B.rows, np, BN, f16) || !make_map(&mb_lo, B.lo, B.rows, np, BN, f16) ||
-      !make_map(&ma_mid, a_mid, A.rows, np, BM, f16) ||
-      !make_map(&mb_mid, b_mid, B.rows, np, BN, f16)) {
-    snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
-    return cudaErrorInvalidValue;
-  }
-  const int nkb = (int)(np / BK);
-  // K chunk drained from TMEM into FP32 registers: 4 k-blocks (256 products per
-  // accumulator pass). np is a multiple of 256, so 4 divides every segment and
-  // the lo-plane weight changes only at a chunk boundary. The tensor core's
-  // FP32 accumulation truncates, and its bias grows with the chunk length: at
-  // N=4096 (FP16X2) 256-wide chunks give a 1.0e-5 density error against the
-  // exact form, 512-wide 2.5e-5 and 2048-wide 7.6e-4, for 3% more time per
-  // product than 512-wide chunks.
-  const int ch = 4;
-  // persistent: one CTA per SM (the shared-memory ring allows no second one)
+int tc_grid(int ntiles) {
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -638,21 +741,90 @@ cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t 
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
       nsm = 1;
   }
-  const int grid = ntiles < nsm ? ntiles : nsm;
-  float* om = static_cast<float*>(out.master);
-  if (kind == KIND_FP16X2)
-    k_gemm_tc<KIND_FP16X2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid, nkb, ch, epi, np, om, out.hi, out.lo, out.mid,
-        x_prev, part, tiles, ntiles, st, step, a_scale, b_scale, zmax);
-  else if (kind == KIND_BF16X3)
-    k_gemm_tc<KIND_BF16X3><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid, nkb, ch, epi, np, om, out.hi, out.lo, out.mid,
-        x_prev, part, tiles, ntiles, st, step, nullptr, nullptr, nullptr);
-  else
-    k_gemm_tc<KIND_BF16X2><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(
-        ma_hi, ma_lo, mb_hi, mb_lo, ma_mid, mb_mid, nkb, ch, epi, np, om, out.hi, out.lo, out.mid,
-        x_prev, part, tiles, ntiles, st, step, nullptr, nullptr, nullptr);
-  return cudaGetLastError();
+  return ntiles < nsm ? ntiles : nsm;
+}
+
+cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size_t errlen) {
+  if (L.ntiles <= 0) return cudaSuccess;
+  const int mode = L.mode;
+  const int kind = mode == SP2_MODE_FP16X2 ? KIND_FP16X2
+                                           : (mode == SP2_MODE_BF16X3 ? KIND_BF16X3 : KIND_BF16X2);
+  const bool f16 = kind == KIND_FP16X2, x3 = kind == KIND_BF16X3;
+  const TcOperand& P = L.P;
+  const TcOperand& Q = L.Q;
+  // the middle planes exist only in BF16X3; elsewhere the hi maps stand in (never read)
+  const uint16_t* p_mid = x3 ? P.mid : P.hi;
+  const uint16_t* q_mid = x3 ? Q.mid : Q.hi;
+  const bool sym_out = L.epi != EPI_PLAIN;
+  if (x3 && (!p_mid || !q_mid || (sym_out && !L.out.mid))) {
+    snprintf(errbuf, errlen, "tcgen05 product: BF16X3 operand without its middle plane");
+    return cudaErrorInvalidValue;
+  }
+  if (sym_out && !L.prev) {
+    snprintf(errbuf, errlen, "tcgen05 product: symmetric epilogue without the previous iterate");
+    return cudaErrorInvalidValue;
+  }
+  // TMA box/stride rules: 16-byte aligned bases, np*2-byte row pitch (np % 256 == 0),
+  // every x coordinate a multiple of 64 elements; tiles never leave their operand.
+  const int64_t np = L.np;
+  if ((reinterpret_cast<uintptr_t>(P.hi) | reinterpret_cast<uintptr_t>(P.lo) |
+       reinterpret_cast<uintptr_t>(Q.hi) | reinterpret_cast<uintptr_t>(Q.lo) |
+       reinterpret_cast<uintptr_t>(p_mid) | reinterpret_cast<uintptr_t>(q_mid)) & 15u ||
+      np % 256 != 0 || P.rows % np != 0 || Q.rows % np != 0 || P.rows % BM != 0 ||
+      Q.rows % BN != 0 || (L.epi == EPI_SYMM && Q.rows != np) ||
+      (L.epi == EPI_SQUARE && P.rows != np) || P.rows > (int64_t)1 << 30) {
+    snprintf(errbuf, errlen, "tcgen05 product: operand alignment/shape violates the TMA rules");
+    return cudaErrorInvalidValue;
+  }
+  KMaps maps;
+  const uint16_t* pp[3] = {P.hi, P.lo, p_mid};
+  const uint16_t* qq[3] = {Q.hi, Q.lo, q_mid};
+  bool mapped = true;
+  for (int i = 0; i < 3; ++i) {
+    mapped = mapped && make_map(&maps.pa[i], pp[i], P.rows, np, BM, f16) &&
+             make_map(&maps.qb[i], qq[i], Q.rows, np, BN, f16);
+    // EPI_SYMM's second half reads X as the left and Y as the right factor
+    mapped = mapped && make_map(&maps.qa[i], qq[i], Q.rows, np, BM, f16) &&
+             make_map(&maps.pb[i], pp[i], P.rows, np, BN, f16);
+  }
+  if (!mapped) {
+    snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
+    return cudaErrorInvalidValue;
+  }
+  KParams p;
+  p.nkb = (int)(np / BK);
+  // K chunk drained from TMEM into FP32 registers: 4 k-blocks (256 products per
+  // accumulator pass). np is a multiple of 256, so 4 divides every segment and
+  // the lo-plane weight changes only at a chunk boundary. The tensor core's
+  // FP32 accumulation truncates, and its bias grows with the chunk length: at
+  // N=4096 (FP16X2) 256-wide chunks give a 1.0e-5 density error against the
+  // exact form, 512-wide 2.5e-5 and 2048-wide 7.6e-4, for 3% more time per
+  // product than 512-wide chunks.
+  p.ch = 4;
+  p.nbase = x3 ? 6 : 3;
+  p.nseg = L.epi == EPI_SYMM ? 2 * p.nbase : p.nbase;
+  p.np = np;
+  p.out = static_cast<float*>(L.out.master);
+  p.out_hi = L.out.hi;
+  p.out_lo = L.out.lo;
+  p.out_mid = L.out.mid;
+  p.prev = L.prev;
+  p.part = L.part;
+  p.tiles = L.tiles;
+  p.ntiles = L.ntiles;
+  p.st = L.st;
+  p.step = L.step;
+  p.p_scale = f16 ? L.p_scale : nullptr;
+  p.q_scale = f16 ? L.q_scale : nullptr;
+  p.o_scale = f16 ? L.o_scale : nullptr;
+  p.zmax = f16 ? L.zmax : nullptr;
+  p.wait_ns = L.tune.wait_ns;
+  p.withhold = L.tune.withhold;
+  // persistent: one CTA per SM (the shared-memory ring allows no second one)
+  const int grid = tc_grid(L.ntiles);
+  if (kind == KIND_FP16X2) return launch_epi<KIND_FP16X2>(L.epi, maps, p, grid, s);
+  if (kind == KIND_BF16X3) return launch_epi<KIND_BF16X3>(L.epi, maps, p, grid, s);
+  return launch_epi<KIND_BF16X2>(L.epi, maps, p, grid, s);
 }
 
 }  // namespace sp2

@@ -458,13 +458,51 @@ __global__ void k_split_scaled(MatBuf m, int64_t per, ScaleBuf sc, int slot) {
   }
 }
 
+// ------------------------------------------------------------ FP16X2 response scales
+// The symmetric response update maps Y to Y X + X Y or Y (I - X) + (I - X) Y,
+// with the spectrum of X in [0, 1]; either way ||Y_{n+1}||_2 <= 2 ||Y_n||_2,
+// and |entry| <= 2-norm <= Frobenius norm. The plane scale of Y_{n+2} is
+// therefore fixed by ||Y_{n+1}||_F before the step that writes it.
+__global__ void k_sym_scale(const Part3* part, const Tile* tiles, int ntiles, int64_t np,
+                            const DevState* st, int step, float* scale_out) {
+  if (st) {
+    const int m = st->stop_at;
+    if ((m != 0 && step > m) || st->abort_flag) return;
+  }
+  const int64_t b = blockIdx.x;
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    if (tiles[t].row0 / np == b) acc += part[t].t2;
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) scale_out[b] = pow2_scale((float)(2.0 * sqrt(fmax(acc, 0.0))));
+}
+
+__global__ void k_fro_part(const float* __restrict__ m, int64_t per, double* part) {
+  const float* x = m + blockIdx.y * per;
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[t];
+    acc += v * v;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_fro_final(const double* part, int nparts, float* scale_out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[blockIdx.x * nparts + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) scale_out[blockIdx.x] = pow2_scale((float)(2.0 * sqrt(acc)));
+}
+
 // ------------------------------------------------------------ contraction
 // out[l,k] = sum_ij P_l[i,j] Q_k[i,j] (Eqs. expectation, direct, dual), FP64
 // accumulation, per-block partials then a fixed-order second pass.
 template <typename T>
 __global__ void k_contract_dense(const T* __restrict__ P, const T* __restrict__ Q, int64_t K,
-                                 int64_t nn, double* part, int nparts) {
-  const int64_t pair = blockIdx.y;
+                                 int64_t nn, double* part, int nparts, int64_t y0) {
+  const int64_t pair = y0 + blockIdx.y;
   const int64_t l = pair / K, k = pair % K;
   const T* p = P + l * nn;
   const T* q = Q + k * nn;
@@ -499,9 +537,11 @@ __device__ __forceinline__ void acc_exact(float& s, float& c, float a, float b) 
 template <int VEC>
 __global__ void __launch_bounds__(256) k_contract_dense_f32(const float* __restrict__ P,
                                                            const float* __restrict__ Q, int64_t K,
-                                                           int64_t nn, double* part, int nparts) {
+                                                           int64_t nn, double* part, int nparts,
+                                                           int64_t y0) {
   const int64_t ktiles = (K + kCtrKT - 1) / kCtrKT;
-  const int64_t l = blockIdx.y / ktiles, k0 = (blockIdx.y % ktiles) * kCtrKT;
+  const int64_t y = y0 + blockIdx.y;
+  const int64_t l = y / ktiles, k0 = (y % ktiles) * kCtrKT;
   const int kn = (int)((K - k0) < kCtrKT ? (K - k0) : kCtrKT);
   const float* p = P + l * nn;
   float s[kCtrKT], c[kCtrKT];
@@ -539,8 +579,8 @@ __global__ void __launch_bounds__(256) k_contract_dense_f32(const float* __restr
 
 template <typename T>
 __global__ void k_contract_diag(const T* __restrict__ P, const T* __restrict__ Q, int64_t K,
-                                int64_t n, double* part, int nparts) {
-  const int64_t pair = blockIdx.y;
+                                int64_t n, double* part, int nparts, int64_t y0) {
+  const int64_t pair = y0 + blockIdx.y;
   const int64_t l = pair / K, k = pair % K;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -647,6 +687,23 @@ cudaError_t launch_split_scaled(MatBuf m, int64_t np, ScaleBuf sc, int slot, cud
   return cudaGetLastError();
 }
 
+cudaError_t launch_sym_scale(const Part3* part, const Tile* tiles, int ntiles, int64_t np,
+                             int64_t batch, const DevState* st, int step, float* scale_out,
+                             cudaStream_t s) {
+  k_sym_scale<<<(unsigned)batch, kRedThreads, 0, s>>>(part, tiles, ntiles, np, st, step, scale_out);
+  return cudaGetLastError();
+}
+
+int fro_nparts() { return 256; }
+
+cudaError_t launch_fro_scale(const float* master, int64_t np, int64_t batch, double* part,
+                             int nparts, float* scale_out, cudaStream_t s) {
+  dim3 grid((unsigned)nparts, (unsigned)batch);
+  k_fro_part<<<grid, kRedThreads, 0, s>>>(master, np * np, part);
+  k_fro_final<<<(unsigned)batch, kRedThreads, 0, s>>>(part, nparts, scale_out);
+  return cudaGetLastError();
+}
+
 // blocks per (l, k) pair: one per 4096 entries, at most 1216 (8 blocks of 256
 // threads per SM on 152 SMs, enough loads in flight for HBM with one pair)
 int contract_nparts(int64_t n, int q_diag) {
@@ -660,34 +717,40 @@ int contract_nparts(int64_t n, int q_diag) {
 cudaError_t launch_contract(const void* P, int64_t L, const void* Q, int64_t K, int64_t n,
                             int dtype, int q_diag, double* part, int nparts, double* out,
                             cudaStream_t s) {
-  dim3 grid((unsigned)nparts, (unsigned)(L * K));
-  if (dtype == SP2_F64) {
-    if (q_diag)
-      k_contract_diag<double><<<grid, 256, 0, s>>>(static_cast<const double*>(P),
-                                                   static_cast<const double*>(Q), K, n, part, nparts);
-    else
-      k_contract_dense<double><<<grid, 256, 0, s>>>(static_cast<const double*>(P),
-                                                    static_cast<const double*>(Q), K, n * n, part,
-                                                    nparts);
-  } else {
-    if (q_diag)
-      k_contract_diag<float><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
-                                                  static_cast<const float*>(Q), K, n, part, nparts);
-    else {
-      // float4 path when every matrix starts on a 16-byte boundary
-      const int64_t nn = n * n;
-      const bool v4 = nn % 4 == 0 && ((reinterpret_cast<uintptr_t>(P) |
-                                       reinterpret_cast<uintptr_t>(Q)) & 15u) == 0;
-      const int64_t ktiles = (K + kCtrKT - 1) / kCtrKT;
-      dim3 g2((unsigned)nparts, (unsigned)(L * ktiles));
-      if (v4)
-        k_contract_dense_f32<4><<<g2, 256, 0, s>>>(static_cast<const float*>(P),
-                                                   static_cast<const float*>(Q), K, nn, part,
-                                                   nparts);
+  // grid rows (one per pair, or per observable and group of kCtrKT perturbations)
+  // go out in launches of at most 65535, the limit of gridDim.y
+  constexpr int64_t kMaxY = 65535;
+  const int64_t nn = n * n;
+  const bool f32_dense = dtype != SP2_F64 && !q_diag;
+  const int64_t ktiles = (K + kCtrKT - 1) / kCtrKT;
+  const int64_t rows = f32_dense ? L * ktiles : L * K;
+  // float4 path when every matrix starts on a 16-byte boundary
+  const bool v4 = nn % 4 == 0 && ((reinterpret_cast<uintptr_t>(P) |
+                                   reinterpret_cast<uintptr_t>(Q)) & 15u) == 0;
+  for (int64_t y0 = 0; y0 < rows; y0 += kMaxY) {
+    const int64_t ny = (rows - y0) < kMaxY ? (rows - y0) : kMaxY;
+    dim3 grid((unsigned)nparts, (unsigned)ny);
+    if (dtype == SP2_F64) {
+      if (q_diag)
+        k_contract_diag<double><<<grid, 256, 0, s>>>(static_cast<const double*>(P),
+                                                     static_cast<const double*>(Q), K, n, part,
+                                                     nparts, y0);
       else
-        k_contract_dense_f32<1><<<g2, 256, 0, s>>>(static_cast<const float*>(P),
+        k_contract_dense<double><<<grid, 256, 0, s>>>(static_cast<const double*>(P),
+                                                      static_cast<const double*>(Q), K, nn, part,
+                                                      nparts, y0);
+    } else if (q_diag) {
+      k_contract_diag<float><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
+                                                  static_cast<const float*>(Q), K, n, part, nparts,
+                                                  y0);
+    } else if (v4) {
+      k_contract_dense_f32<4><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
                                                    static_cast<const float*>(Q), K, nn, part,
-                                                   nparts);
+                                                   nparts, y0);
+    } else {
+      k_contract_dense_f32<1><<<grid, 256, 0, s>>>(static_cast<const float*>(P),
+                                                   static_cast<const float*>(Q), K, nn, part,
+                                                   nparts, y0);
     }
   }
   k_contract_final<<<(unsigned)(L * K), 256, 0, s>>>(part, nparts, out);

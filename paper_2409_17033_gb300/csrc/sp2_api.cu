@@ -34,6 +34,7 @@ struct sp2_handle_s {
   std::map<std::string, TileList> tiles;
   DevState* d_state = nullptr;
   DevState* h_state = nullptr;  // pinned mirror
+  TcTuning tune;                // product-kernel launch settings (sp2_set_option)
   std::vector<cudaEvent_t> events;  // pool for time_kernels (start/stop pairs)
 
   // X_n history kept for sp2_adjoint
@@ -223,7 +224,7 @@ int tile_list(sp2_handle_t h, int mode, int64_t rows, int64_t np, bool upper, co
     for (int64_t cn = 0; cn < nn; ++cn)
       for (int64_t m = g0; m < g0 + gs; ++m) {
         const int64_t r0 = m * bm, c0 = cn * bn;
-        if (upper && r0 > c0 + bn - 1) continue;
+        if (upper && r0 % np > c0 + bn - 1) continue;   // row within its batch entry
         v.push_back(Tile{(int)r0, (int)c0});
       }
   }
@@ -288,6 +289,18 @@ int64_t timed_count(const Ctx& c, int m) {
 // tensor products per logical product: 3 (two planes), 6 (BF16X3), 1 (plain)
 double k_mult(int mode) { return n_planes(mode) == 3 ? 6.0 : (split_mode(mode) ? 3.0 : 1.0); }
 
+// settings shared by every product launch of a context: mode, padded size, state,
+// partials and the handle's launch settings
+int tc_common(Ctx& c, TcLaunch* L, int ntiles) {
+  L->mode = c.mode;
+  L->np = c.np;
+  L->st = c.st;
+  L->part = c.part;
+  L->ntiles = ntiles;
+  L->tune = c.h->tune;
+  return SP2_OK;
+}
+
 // X_{n+1} = sigma_n>0 ? X_n^2 : 2 X_n - X_n^2, with trace partials; returns #partials
 int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* nparts) {
   sp2_handle_t h = c.h;
@@ -296,6 +309,8 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   TRY(tile_list(h, c.mode, c.np, c.np, true, &tl, &nt));
   int bm, bn;
   tile_shape(c.mode, &bm, &bn);
+  TcLaunch L;   // workspace first: nothing is allocated inside the timed interval
+  if (split_mode(c.mode)) TRY(tc_common(c, &L, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.timing) {
     TRY(ev_pair(c, &e0, &e1));
@@ -303,10 +318,14 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   }
   if (split_mode(c.mode)) {
     char eb[256] = {0};
-    TcOperand a{xin.hi, xin.lo, c.np, xin.mid};
-    cudaError_t e = launch_gemm_tc(c.mode, EPI_SQUARE, a, a, c.np, xout,
-                                   static_cast<const float*>(xin.master), c.part, tl, nt, c.st,
-                                   step, nullptr, nullptr, h->stream, eb, sizeof eb);
+    L.epi = EPI_SQUARE;
+    L.P = TcOperand{xin.hi, xin.lo, c.np, xin.mid};
+    L.Q = L.P;
+    L.out = xout;
+    L.prev = static_cast<const float*>(xin.master);
+    L.tiles = tl;
+    L.step = step;
+    cudaError_t e = launch_gemm_tc(L, h->stream, eb, sizeof eb);
     if (e != cudaSuccess) return fail(h, SP2_ECUDA, "square product: %s %s", cudaGetErrorString(e), eb);
   } else {
     CK(launch_gemm_simt(c.mode, EPI_SQUARE, xin.master, c.np, xin.master, c.np, xout.master,
@@ -324,33 +343,88 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   return SP2_OK;
 }
 
-// Y_{n+1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n) for a batch of Y
+// Y_{n+1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n) for a batch of Y.
+// Default: Z = Y X (tcgen05 EPI_PLAIN in split modes, CUDA cores otherwise), then
+// the transpose-add kernel. With the handle's fused_response option (split modes):
+// one tcgen05 launch over the upper tiles of every batch entry with the update in
+// its epilogue (EPI_SYMM, no Z); in FP16X2 the output planes then take the scale
+// sc.yscale[slot_out], fixed beforehand from ||Y_n||_F, and the scale of Y_{n+2}
+// (slot_in) follows from this launch's partials.
 int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout, int64_t batch,
                   int step, const ScaleBuf& sc, int slot_in, int slot_out) {
   sp2_handle_t h = c.h;
   const int64_t rows = batch * c.np;
-  void* z;
-  TRY(ws(h, "Z", (size_t)rows * c.np * master_size(c.mode), &z));
+  const bool split = split_mode(c.mode);
+  const bool fused = split && h->tune.fused_response;
   const Tile* tl;
   int nt;
-  TRY(tile_list(h, c.mode, rows, c.np, false, &tl, &nt));
+  TRY(tile_list(h, c.mode, rows, c.np, fused, &tl, &nt));
   int bm, bn;
   tile_shape(c.mode, &bm, &bn);
+  // workspace first: nothing is allocated inside the timed interval
+  TcLaunch L;
+  void* yp = nullptr;
+  void* z = nullptr;
+  if (fused) {
+    TRY(ws(h, "ypart", (size_t)nt * sizeof(Part3), &yp));
+  } else {
+    TRY(ws(h, "Z", (size_t)rows * c.np * master_size(c.mode), &z));
+  }
+  if (split) TRY(tc_common(c, &L, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.timing) {
     TRY(ev_pair(c, &e0, &e1));
     CK(cudaEventRecord(e0, h->stream));
   }
   const bool f16 = c.mode == SP2_MODE_FP16X2;
-  if (f16) CK(cudaMemsetAsync(sc.zmax, 0, sizeof(float) * batch, h->stream));
-  if (split_mode(c.mode)) {
+  if (fused) {
     char eb[256] = {0};
-    TcOperand a{yin.hi, yin.lo, rows, yin.mid}, b{x.hi, x.lo, c.np, x.mid};
+    L.epi = EPI_SYMM;
+    L.P = TcOperand{yin.hi, yin.lo, rows, yin.mid};
+    L.Q = TcOperand{x.hi, x.lo, c.np, x.mid};
+    L.out = yout;
+    L.prev = static_cast<const float*>(yin.master);
+    L.part = static_cast<Part3*>(yp);
+    L.tiles = tl;
+    L.step = step;
+    if (f16) {
+      L.p_scale = sc.yscale + slot_in * sc.B;
+      L.o_scale = sc.yscale + slot_out * sc.B;
+    }
+    cudaError_t e = launch_gemm_tc(L, h->stream, eb, sizeof eb);
+    if (e != cudaSuccess) return fail(h, SP2_ECUDA, "response product: %s %s", cudaGetErrorString(e), eb);
+    if (c.timing) {
+      CK(cudaEventRecord(e1, h->stream));
+      c.timed.push_back({step, 0});
+    }
+    if (f16) {
+      CK(launch_sym_scale(static_cast<Part3*>(yp), tl, nt, c.np, batch, c.st, step,
+                          sc.yscale + slot_in * sc.B, h->stream));
+      c.kernels++;
+    }
+    c.launches++;
+    c.kernels++;
+    // the update takes Y X + X Y over the upper tiles: K = 2 np per output tile
+    c.flops += 2.0 * bm * bn * (double)c.np * 2.0 * k_mult(c.mode) * nt;
+    c.alg += 2.0 * (double)batch * (double)c.n * (double)c.n * (double)c.n * k_mult(c.mode);
+    return SP2_OK;
+  }
+  if (split) {
+    char eb[256] = {0};
+    if (f16) CK(cudaMemsetAsync(sc.zmax, 0, sizeof(float) * batch, h->stream));
+    L.epi = EPI_PLAIN;
+    L.P = TcOperand{yin.hi, yin.lo, rows, yin.mid};
+    L.Q = TcOperand{x.hi, x.lo, c.np, x.mid};
     MatBuf zo;
     zo.master = z;
-    cudaError_t e = launch_gemm_tc(c.mode, EPI_PLAIN, a, b, c.np, zo, nullptr, c.part, tl, nt, c.st,
-                                   step, f16 ? sc.yscale + slot_in * sc.B : nullptr,
-                                   f16 ? sc.zmax : nullptr, h->stream, eb, sizeof eb);
+    L.out = zo;
+    L.tiles = tl;
+    L.step = step;
+    if (f16) {
+      L.p_scale = sc.yscale + slot_in * sc.B;
+      L.zmax = sc.zmax;
+    }
+    cudaError_t e = launch_gemm_tc(L, h->stream, eb, sizeof eb);
     if (e != cudaSuccess) return fail(h, SP2_ECUDA, "response product: %s %s", cudaGetErrorString(e), eb);
   } else {
     CK(launch_gemm_simt(c.mode, EPI_PLAIN, yin.master, rows, x.master, c.np, z, nullptr, c.part,
@@ -367,6 +441,20 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
   c.kernels += 2;
   c.flops += 2.0 * bm * bn * (double)c.np * k_mult(c.mode) * nt;
   c.alg += 2.0 * (double)batch * (double)c.n * (double)c.n * (double)c.n * k_mult(c.mode);
+  return SP2_OK;
+}
+
+// FP16X2: the plane scale of the first response step's output (slot `slot_out`)
+// from the Frobenius norms of the batch in `m` (the response update at most
+// doubles the 2-norm)
+int first_sym_scale(Ctx& c, const MatBuf& m, int64_t batch, const ScaleBuf& sc, int slot_out) {
+  sp2_handle_t h = c.h;
+  const int np_ = fro_nparts();
+  void* fp;
+  TRY(ws(h, "fro.part", (size_t)batch * np_ * sizeof(double), &fp));
+  CK(launch_fro_scale(static_cast<const float*>(m.master), c.np, batch, static_cast<double*>(fp),
+                      np_, sc.yscale + slot_out * sc.B, h->stream));
+  c.kernels += 2;
   return SP2_OK;
 }
 
@@ -531,6 +619,7 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
     if (f16) {
       CK(launch_split_scaled(Y[1], np, sc, 1, h->stream));
       c.kernels += 2;
+      if (h->tune.fused_response) TRY(first_sym_scale(c, Y[1], ybatch, sc, 0));
     }
   }
 
@@ -699,6 +788,7 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
   if (f16) {
     CK(launch_split_scaled(G[gs], np, sc, gs, h->stream));
     c.kernels += 2;
+    if (h->tune.fused_response) TRY(first_sym_scale(c, G[gs], batch, sc, 1 - gs));
   }
   // segment buffers X_{s0+1} .. X_{s0+k-1}; X_{s0} is read from its checkpoint in place
   // (the master) with its planes split into seg[0], or taken as the kept planes
@@ -747,6 +837,12 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
   CK(launch_copy_out(G[gs], n, np, batch, mode, hs.beta, outd, out_dtype, h->stream));
   c.kernels++;
   c.st = h->d_state;
+  // the adjoint's product launches report a timed-out device wait in their own state
+  CK(cudaMemcpyAsync(&h->h_state->abort_flag, &ast->abort_flag, sizeof(int),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->h_state->abort_flag)
+    return fail(h, SP2_ETIMEOUT, "a device-side wait timed out in a product kernel (adjoint)");
   return SP2_OK;
 }
 
@@ -797,6 +893,8 @@ int fprod(Ctx& c, FMat& C, const FMat& L, const FMat& R) {
   TRY(tile_list(h, c.mode, c.np, c.np, false, &tl, &nt));
   int bm, bn;
   tile_shape(c.mode, &bm, &bn);
+  TcLaunch T;   // workspace first: nothing is allocated inside the timed interval
+  if (split_mode(c.mode)) TRY(tc_common(c, &T, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.timing) {
     TRY(ev_pair(c, &e0, &e1));
@@ -806,10 +904,18 @@ int fprod(Ctx& c, FMat& C, const FMat& L, const FMat& R) {
     const bool f16 = c.mode == SP2_MODE_FP16X2;
     if (f16) CK(cudaMemsetAsync(C.amax, 0, sizeof(float), h->stream));
     char eb[256] = {0};
-    TcOperand a{L.m.hi, L.m.lo, c.np, L.m.mid}, b{R.m.hi, R.m.lo, c.np, R.m.mid};
-    cudaError_t e = launch_gemm_tc(c.mode, EPI_PLAIN, a, b, c.np, C.m, nullptr, c.part, tl, nt,
-                                   c.st, 0, f16 ? L.scale : nullptr, f16 ? C.amax : nullptr,
-                                   h->stream, eb, sizeof eb, f16 ? R.scale : nullptr);
+    T.epi = EPI_PLAIN;
+    T.P = TcOperand{L.m.hi, L.m.lo, c.np, L.m.mid};
+    T.Q = TcOperand{R.m.hi, R.m.lo, c.np, R.m.mid};
+    T.out = C.m;
+    T.tiles = tl;
+    T.step = 0;
+    if (f16) {
+      T.p_scale = L.scale;
+      T.q_scale = R.scale;
+      T.zmax = C.amax;
+    }
+    cudaError_t e = launch_gemm_tc(T, h->stream, eb, sizeof eb);
     if (e != cudaSuccess) return fail(h, SP2_ECUDA, "finite-T product: %s %s", cudaGetErrorString(e), eb);
   } else {
     CK(launch_gemm_simt(c.mode, EPI_PLAIN, L.m.master, c.np, R.m.master, c.np, C.m.master, nullptr,
@@ -913,6 +1019,25 @@ int sp2_set_stream(sp2_handle_t h, void* stream) {
   if (!h) return SP2_EINVAL;
   h->stream = static_cast<cudaStream_t>(stream);
   return SP2_OK;
+}
+
+int sp2_set_option(sp2_handle_t h, int option, int64_t value) {
+  if (!h) return SP2_EINVAL;
+  switch (option) {
+    case SP2_OPTION_WAIT_LIMIT_NS:
+      if (value < 1000 || value > (int64_t)60000000000ll)
+        return fail(h, SP2_EINVAL, "wait limit %lld ns outside [1e3, 6e10]", (long long)value);
+      h->tune.wait_ns = (unsigned long long)value;
+      return SP2_OK;
+    case SP2_OPTION_WITHHOLD_LOAD:
+      h->tune.withhold = value != 0 ? 1 : 0;
+      return SP2_OK;
+    case SP2_OPTION_FUSED_RESPONSE:
+      h->tune.fused_response = value != 0 ? 1 : 0;
+      return SP2_OK;
+    default:
+      return fail(h, SP2_EINVAL, "unknown option %d", option);
+  }
 }
 
 const char* sp2_last_error(sp2_handle_t h) { return h ? h->err.c_str() : "null handle"; }

@@ -108,6 +108,7 @@ struct ScaleBuf {
 enum Epi : int {
   EPI_SQUARE = 0,   // out = sigma>0 ? C : 2 X - C, symmetric (upper tiles, mirrored), traces
   EPI_PLAIN = 1,    // out = C (fp32/fp64 Z), all tiles
+  EPI_SYMM = 2,     // out = sigma>0 ? YX+XY : 2Y - (YX+XY), symmetric batch (upper tiles, mirrored)
 };
 
 // Per-block partial sums written by the kernels that produce an X_{n+1}:
@@ -182,22 +183,54 @@ cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, c
                              cudaStream_t s);
 void simt_tile_shape(int mode, int* bm, int* bn);
 
-// tcgen05 split-precision (BF16X2 / FP16X2)
+// tcgen05 split-precision (BF16X2 / FP16X2 / BF16X3)
 struct TcOperand {   // hi/lo (and BF16X3 mid) planes of a stacked operand, rows x np
-  const uint16_t* hi;
-  const uint16_t* lo;
-  int64_t rows;
+  const uint16_t* hi = nullptr;
+  const uint16_t* lo = nullptr;
+  int64_t rows = 0;
   const uint16_t* mid = nullptr;
 };
-// a_scale (FP16X2, EPI_PLAIN): per batch entry of A, the plane scale to divide
-// out; b_scale (FP16X2, nullable): the plane scale of B; zmax (FP16X2,
-// EPI_PLAIN): per batch entry, receives max |Z|.
-cudaError_t launch_gemm_tc(int mode, int epi, TcOperand A, TcOperand B, int64_t np, MatBuf out,
-                           const float* x_prev, Part3* part, const Tile* tiles, int ntiles,
-                           DevState* st, int step, const float* a_scale, float* zmax,
-                           cudaStream_t s, char* errbuf, size_t errlen,
-                           const float* b_scale = nullptr);
+// Launch settings of the product kernel that are not part of the arithmetic.
+struct TcTuning {
+  unsigned long long wait_ns = 2000000000ull;  // limit of every mbarrier wait
+  int withhold = 0;    // test hook: the first TMA load of CTA 0 is never issued
+  int fused_response = 0;  // response step as one EPI_SYMM launch (else EPI_PLAIN + transpose-add)
+};
+// One product launch: C = P Q (EPI_SQUARE: P = Q = X; EPI_PLAIN: P = stacked A,
+// Q = symmetric B; EPI_SYMM: P = stacked symmetric Y, Q = X, C = Y X + X Y).
+struct TcLaunch {
+  int mode = 0;
+  int epi = 0;
+  TcOperand P, Q;
+  int64_t np = 0;
+  MatBuf out;                      // master + planes (planes only for the symmetric epilogues)
+  const float* prev = nullptr;     // EPI_SQUARE: X_n master; EPI_SYMM: Y_n master
+  Part3* part = nullptr;           // per-tile partials (>= ntiles)
+  const Tile* tiles = nullptr;
+  int ntiles = 0;
+  DevState* st = nullptr;
+  int step = 0;
+  const float* p_scale = nullptr;  // FP16X2: per batch entry of P, the plane scale to divide out
+  const float* q_scale = nullptr;  // FP16X2: the plane scale of Q (nullable)
+  const float* o_scale = nullptr;  // FP16X2 EPI_SYMM: per batch entry, scale of the output planes
+  float* zmax = nullptr;           // FP16X2 EPI_PLAIN: per batch entry, receives max |C|
+  TcTuning tune;
+};
+cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size_t errlen);
 void tc_tile_shape(int* bm, int* bn);
+int tc_grid(int ntiles);            // CTAs of a launch over ntiles tiles
+
+// FP16X2 scale of the next symmetric response step: per batch entry, the sum of
+// the EPI_SYMM tile partials (||Y_{n+1}||_F^2) and the plane scale of Y_{n+2},
+// pow2_scale(2 ||Y_{n+1}||_F) (|Y_{n+2}|_max <= ||Y_{n+2}||_2 <= 2 ||Y_{n+1}||_2).
+// No-op when the recursion stopped before `step`.
+cudaError_t launch_sym_scale(const Part3* part, const Tile* tiles, int ntiles, int64_t np,
+                             int64_t batch, const DevState* st, int step, float* scale_out,
+                             cudaStream_t s);
+// FP16X2: the same bound from a batch's masters (the first response step)
+cudaError_t launch_fro_scale(const float* master, int64_t np, int64_t batch, double* part,
+                             int nparts, float* scale_out, cudaStream_t s);
+int fro_nparts();
 
 // finite temperature (fermi_kernels.cu)
 // out = z1 (Z1 + Z1^T) + z2 (Z2 + Z2^T) + a A + id I on the padded np x np

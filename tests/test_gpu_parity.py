@@ -371,6 +371,27 @@ def test_response_contract_dense_and_diagonal(sp2):
         assert np.allclose(o32, ref32, rtol=1e-12, atol=1e-10)
 
 
+@pytest.mark.parametrize("case", ["f64_dense", "f32_diag", "f32_dense"])
+def test_response_contract_beyond_65535_grid_rows(sp2, case):
+    """More (observable, perturbation) work rows than one launch's gridDim.y
+    (65535) holds: the rows go out in several launches, and every pair must
+    equal the FP64 einsum of the same values."""
+    rng = np.random.default_rng(5)
+    if case == "f64_dense":
+        L, K, n, diag, dt = 7, 10000, 16, False, torch.float64
+    elif case == "f32_diag":
+        L, K, n, diag, dt = 7, 10000, 16, True, torch.float32
+    else:   # FP32 dense groups 8 perturbations per row: L * ceil(K / 8) rows
+        L, K, n, diag, dt = 70000, 1, 8, False, torch.float32
+    P = rng.standard_normal((L, n, n)).astype(np.float32).astype(np.float64)
+    Q = rng.standard_normal((K, n) if diag else (K, n, n)).astype(np.float32).astype(np.float64)
+    out = host(sp2.response_contract(cuda(P, dt), cuda(Q, dt), diag_only=diag))
+    ref = (np.einsum("lii,ki->lk", P, Q) if diag else
+           np.einsum("lij,kij->lk", P, Q))
+    assert out.shape == (L, K)
+    assert np.allclose(out, ref, rtol=1e-12, atol=1e-10)
+
+
 def test_diagonal_perturbations(sp2):
     """Site-potential perturbations passed as diagonals equal the dense form."""
     tb = workloads.tight_binding(512, seed=0)

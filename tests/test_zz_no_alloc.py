@@ -54,6 +54,27 @@ def test_noalloc_matches_handle_entry_point_twice(lib, dtype, diag):
         assert np.allclose(got, ref, rtol=1e-12, atol=1e-10), f"call {call}"
 
 
+@pytest.mark.parametrize("case", ["clamped_partials", "most_pairs"])
+def test_noalloc_at_its_limits(lib, case):
+    """The two ends of the fixed partial-sum array: a dense FP32 case whose usual
+    partial count (256 per pair at N=1024) times its 32 x 32 pairs exceeds the
+    array, so every pair gets fewer partials; and the largest pair count the
+    entry point accepts (L * K = 65535) with diagonal perturbations. Both twice
+    in a row against the handle-based entry point."""
+    import paper_2409_17033_gb300 as sp2
+    rng = np.random.default_rng(11)
+    if case == "clamped_partials":
+        L, K, n, diag, dt = 32, 32, 1024, False, torch.float32
+    else:
+        L, K, n, diag, dt = 5, 13107, 64, True, torch.float64
+    P = torch.from_numpy(rng.standard_normal((L, n, n))).to(dt).cuda()
+    Q = torch.from_numpy(rng.standard_normal((K, n) if diag else (K, n, n))).to(dt).cuda()
+    ref = sp2.response_contract(P, Q, diag_only=diag).cpu().numpy()
+    for call in range(2):
+        got = _noalloc(lib, P, Q, diag)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-10), f"call {call}"
+
+
 def test_noalloc_rejects_bad_arguments(lib):
     from paper_2409_17033_gb300 import _lib
     P = torch.zeros((1, 4, 4), dtype=torch.float64, device="cuda")
