@@ -53,6 +53,50 @@ def test_scf_fp64_matches_oracle(pkg, small, mixer):
     assert np.allclose(res[:k], res_or[:k], rtol=1e-6 if mixer == "linear" else 1e-3, atol=1e-10)
 
 
+@pytest.mark.parametrize("net", ["random", "exact_correction"])
+def test_scf_mlp_mixer_matches_oracle_step_by_step(pkg, small, net):
+    """The learned mixer q <- q + alpha r + ||r|| MLP(r/||r||) on the GPU (FP64
+    responses, FP32 network, no bfloat16) against the oracle's MLP branch of
+    scf_iterate with the same weights, residual by residual. "random": a small
+    random network (the mixer stays contractive); "exact_correction": the ReLU
+    pair that represents (I - chi0 K)^(-1) - alpha I exactly, so the residual
+    drops to the FP32 network's rounding in one step."""
+    tb, chi0, K, Vx = small
+    ns = chi0.shape[0]
+    alpha = 0.3
+    if net == "random":
+        rng = np.random.default_rng(4)
+        W1 = rng.standard_normal((32, ns)) / np.sqrt(ns)
+        W2 = 0.05 * rng.standard_normal((ns, 32)) / np.sqrt(32)
+        tol, cap = 1e-8, 200
+    else:
+        C = np.linalg.inv(np.eye(ns) - chi0 @ K) - alpha * np.eye(ns)
+        W1 = np.vstack([np.eye(ns), -np.eye(ns)])
+        W2 = np.hstack([C, -C])
+        tol, cap = 1e-5, 10
+    W1 = W1.astype(np.float32)
+    W2 = W2.astype(np.float32)
+    H = torch.from_numpy(tb.H).cuda()
+    q, res, its, _ = pkg.sp2_scf_response(
+        H, tb.nocc, 4, K, Vx, mixer="mlp", alpha=alpha, tol=tol, max_iter=cap,
+        W1=torch.from_numpy(W1).cuda(), W2=torch.from_numpy(W2).cuda(), bf16_infer=False,
+        mode="fp64", idem_tol=1e-13)
+    q_or, res_or = scf.scf_iterate(chi0, K, Vx, mixer="mlp", alpha=alpha, tol=tol, max_iter=cap,
+                                   mlp=(W1.astype(np.float64), W2.astype(np.float64)))
+    assert abs(its - len(res_or)) <= 1
+    if net == "exact_correction":
+        # one step to the solution on both sides; the remaining residual is each
+        # side's rounding of the network (FP32 weights: ~1e-8 oracle, ~1e-7 GPU)
+        assert its == 2 and len(res_or) == 2
+        assert res[0] == pytest.approx(res_or[0], rel=1e-9)
+        assert res[1] < 1e-6 and res_or[1] < 1e-6
+    else:
+        k = min(its, len(res_or))
+        # the network runs in FP32 on the GPU: each step's correction carries ~1e-7
+        assert np.allclose(res[:k], res_or[:k], rtol=1e-5, atol=1e-9)
+    assert rel(q, q_or) < 1e-6
+
+
 def test_scf_split_precision(pkg, small):
     tb, chi0, K, Vx = small
     H = torch.from_numpy(tb.H).float().cuda()

@@ -140,3 +140,65 @@ def test_finite_t_chi0_and_scf_duality(small):
     primal = obs @ scf.scf_exact(c0, K, Vx).T
     dual = scf.scf_exact(c0, K, obs) @ Vx.T
     assert np.allclose(primal, dual, rtol=1e-10, atol=1e-12 * np.abs(primal).max())
+
+
+# ------------------------------------------------------------ the learned mixer
+# The MLP mixer of scf_iterate: q <- q + alpha r + ||r|| MLP(r / ||r||) with
+# MLP(x) = W2 relu(W1 x), no biases.
+
+def test_mlp_mixer_with_zero_network_is_linear_mixing(small):
+    """An MLP whose output layer is zero adds nothing: the residual history and
+    the iterate equal plain linear mixing with the same alpha, step for step."""
+    tb, e, V, chi0, K, Vx = small
+    ns = chi0.shape[0]
+    rng = np.random.default_rng(1)
+    W1 = rng.standard_normal((16, ns))
+    W2 = np.zeros((ns, 16))
+    ql, rl = scf.scf_iterate(chi0, K, Vx, mixer="linear", alpha=0.3, tol=1e-9, max_iter=40)
+    qm, rm = scf.scf_iterate(chi0, K, Vx, mixer="mlp", alpha=0.3, tol=1e-9, max_iter=40,
+                             mlp=(W1, W2))
+    assert rm == rl
+    assert np.array_equal(qm, ql)
+
+
+# Two sites, one field, no interaction (K = 0), chi0 = I/2, V = [2, -2]: the
+# output charges are q_out = [1, -1] whatever q is. alpha = 0.3,
+# W1 = [[1, 0.5], [0, 1]], W2 = [[0.2, 0.6], [-0.4, 0.8]]. Worked by hand
+# (||r|| MLP(r/||r||) = MLP(r), the map being positively homogeneous):
+#   it 0: q = 0, r = [1, -1], residual ||r|| / ||q_out(0)|| = 1;
+#         W1 r = [0.5, -1] -> relu [0.5, 0] -> W2 . = [0.1, -0.2];
+#         q = 0.3 r + [0.1, -0.2] = [0.4, -0.5]
+#   it 1: r = [0.6, -0.5], residual sqrt(0.61 / 2) = sqrt(0.305);
+#         W1 r = [0.35, -0.5] -> relu [0.35, 0] -> W2 . = [0.07, -0.14];
+#         q = [0.4, -0.5] + [0.18, -0.15] + [0.07, -0.14] = [0.65, -0.79]
+#   it 2: r = [0.35, -0.21], residual sqrt(0.1666 / 2) = sqrt(0.0833)
+_HAND = dict(chi0=np.eye(2) / 2, K=np.zeros((2, 2)), V=np.array([[2.0, -2.0]]),
+             W1=np.array([[1.0, 0.5], [0.0, 1.0]]), W2=np.array([[0.2, 0.6], [-0.4, 0.8]]))
+
+
+def test_mlp_mixer_two_steps_worked_by_hand():
+    h = _HAND
+    kw = dict(mixer="mlp", alpha=0.3, tol=0.0, mlp=(h["W1"], h["W2"]))
+    q1, r1 = scf.scf_iterate(h["chi0"], h["K"], h["V"], max_iter=1, **kw)
+    q2, r2 = scf.scf_iterate(h["chi0"], h["K"], h["V"], max_iter=2, **kw)
+    _, r3 = scf.scf_iterate(h["chi0"], h["K"], h["V"], max_iter=3, **kw)
+    assert np.allclose(q1, [[0.4, -0.5]], rtol=0, atol=1e-15)
+    assert np.allclose(q2, [[0.65, -0.79]], rtol=0, atol=1e-15)
+    assert np.allclose(r3, [1.0, np.sqrt(0.305), np.sqrt(0.0833)], rtol=1e-14, atol=0)
+
+
+def test_mlp_mixer_with_the_exact_correction_converges_in_one_step(small):
+    """For q_out(q) = chi0 (V + K q) the exact step from q = 0 is
+    q* = (I - chi0 K)^(-1) r_0 = alpha r_0 + C r_0 with C = (I - chi0 K)^(-1) - alpha I.
+    The ReLU pair W1 = [I; -I], W2 = [C, -C] represents C exactly
+    (relu(x) - relu(-x) = x), so one mixer step lands on the closed-form solution."""
+    tb, e, V, chi0, K, Vx = small
+    ns = chi0.shape[0]
+    alpha = 0.3
+    C = np.linalg.inv(np.eye(ns) - chi0 @ K) - alpha * np.eye(ns)
+    W1 = np.vstack([np.eye(ns), -np.eye(ns)])
+    W2 = np.hstack([C, -C])
+    q, res = scf.scf_iterate(chi0, K, Vx, mixer="mlp", alpha=alpha, tol=1e-11, max_iter=5,
+                             mlp=(W1, W2))
+    assert len(res) == 2 and res[1] < 1e-11
+    assert np.allclose(q, scf.scf_exact(chi0, K, Vx), rtol=1e-10, atol=1e-13)
