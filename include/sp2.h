@@ -31,12 +31,28 @@
  *
  * Pointers may be device memory (cudaMalloc, torch tensors) or host memory
  * (pageable or pinned); host buffers are staged through handle-owned device
- * memory with copies on the handle's stream, and the call then returns only
- * after the result is back in host memory. The library never frees or keeps
- * caller memory. All device work is enqueued on the handle's stream; when
- * every buffer is device memory the call still synchronises that stream
- * once per SP2 iteration batch (it reads the branch/stop state), so results
- * are complete when the call returns.
+ * memory with copies on the handle's stream. The library never frees or keeps
+ * caller memory.
+ *
+ * Asynchrony. All device work is enqueued on the handle's stream. The SP2
+ * step loop never drains that stream: the host reads the branch/stop state
+ * from pinned snapshots at most 8 steps behind the step it enqueues (those
+ * steps become no-ops on the device once the recursion has stopped), so the
+ * stop, M and the kept iterate are known when sp2_density, sp2_response and
+ * sp2_susceptibility return, while the remaining device work (the last steps,
+ * the adjoint of a backward susceptibility, output copies) may still run.
+ *   - info == NULL and every output in device memory: the call returns without
+ *     waiting; outputs are valid once the stream has reached them, and
+ *     sp2_synchronize(h, info) waits, reports the call's final status and fills
+ *     its info.
+ *   - info != NULL, or an output in host memory: the call waits for its work
+ *     and returns the final status with info filled (synchronous use).
+ * sp2_adjoint behaves the same way. sp2_fermi, sp2_nonorth_susceptibility,
+ * sp2_scf_response and response_contract always return after their work is
+ * done. Statuses known when a call returns (bad arguments, ENOCONV, a NaN
+ * found by the stop test, a timed-out wait seen by the step loop) are returned
+ * at once; a timed-out wait in later work of the call (the adjoint) is
+ * reported by sp2_synchronize.
  *
  * Internal working storage (padded copies, X ping-pong buffers, split planes,
  * the X_n checkpoints of the adjoint, reduction partials) is owned by the
@@ -129,6 +145,15 @@ typedef struct {
   int keep_history;    /* sp2_density: keep the X_n checkpoints for a later sp2_adjoint */
   int time_kernels;    /* 1: bracket every product-kernel launch with CUDA events on the
                           handle's stream and report their summed duration in sp2_info */
+  double tail_f;       /* split modes, > 0: split-tail arithmetic (the mixed-precision use the
+                          paper suggests in Sec. VI.B: low precision in the bulk of the
+                          iterations, higher precision in the last ones). Step n uses the hi
+                          planes alone (one 16-bit product, FP32 accumulation) while
+                          f = ||X - X^2||_F^2 of the last measured iterate exceeds tail_f, and
+                          the split products from the first step where it does not on (the
+                          decision is made on the device; the adjoint follows the same steps).
+                          With SP2_MODE_BF16X2 this is the bfloat16 bulk / split tail form.
+                          0 (default): split products in every step. */
 } sp2_opts;
 
 typedef struct {
@@ -155,6 +180,9 @@ typedef struct {
   int refine_iter;                    /* sp2_scf_response: first iteration (0-based) computed
                                          in refine_mode, -1 if none; sp2_nonorth_susceptibility:
                                          Newton-Schulz iterations of S^(-1/2) */
+  int tail_single_steps;              /* split-tail mode: steps 1..M that used the hi planes
+                                         alone (executed_flops and algorithmic_flops count
+                                         split products for every step) */
 } sp2_info;
 
 typedef struct sp2_handle_s* sp2_handle_t;
@@ -226,6 +254,15 @@ int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad,
 
 /* Release a kept X_n history (device memory) without destroying the handle. */
 int sp2_release_history(sp2_handle_t h);
+
+/* Wait for the handle's stream and complete the last call that returned
+ * without waiting (see "Asynchrony" above): returns that call's final status
+ * (e.g. SP2_ETIMEOUT for a timed-out wait in its adjoint) and fills *info
+ * (nullable) as the synchronous form of the call would have. With no such call
+ * pending it waits for the stream, zeroes *info and returns SP2_OK. Only the
+ * most recent call is reported: a call made before the previous one was
+ * synchronised discards the previous one's report (its work still runs). */
+int sp2_synchronize(sp2_handle_t h, sp2_info* info);
 
 /* Finite electronic temperature (Sec. V.B): the Fermi-Dirac density matrix
  *     D = f(H) = (exp((H - mu I) / kT) + I)^(-1)

@@ -7,11 +7,12 @@ there is no CPU fallback.
 """
 from .api import (Handle, SP2Error, make_opts, mlp_forward, mlp_loss_grad, mlp_train,
                   response_contract, sp2_adjoint, sp2_density, sp2_fermi,
-                  sp2_nonorth_susceptibility, sp2_response, sp2_scf_response, sp2_susceptibility)
+                  sp2_nonorth_susceptibility, sp2_response, sp2_scf_response, sp2_susceptibility,
+                  synchronize)
 from .autograd import SP2Density, sp2_density_autograd
 
 __all__ = ["Handle", "SP2Error", "make_opts", "sp2_density", "sp2_response",
            "sp2_susceptibility", "sp2_adjoint", "sp2_fermi", "sp2_nonorth_susceptibility",
            "sp2_scf_response", "mlp_forward",
            "mlp_loss_grad", "mlp_train", "response_contract", "SP2Density",
-           "sp2_density_autograd"]
+           "sp2_density_autograd", "synchronize"]

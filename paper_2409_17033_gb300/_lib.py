@@ -45,6 +45,7 @@ class Opts(C.Structure):
         ("ckpt_k", C.c_int),
         ("keep_history", C.c_int),
         ("time_kernels", C.c_int),
+        ("tail_f", C.c_double),
     ]
 
 
@@ -69,6 +70,7 @@ class Info(C.Structure):
         ("product_launches_timed", C.c_int64),
         ("ckpt_k", C.c_int),
         ("refine_iter", C.c_int),
+        ("tail_single_steps", C.c_int),
     ]
 
     def to_dict(self) -> dict:
@@ -93,6 +95,7 @@ class Info(C.Structure):
             "product_launches_timed": int(self.product_launches_timed),
             "ckpt_k": int(self.ckpt_k),
             "refine_iter": int(self.refine_iter),
+            "tail_single_steps": int(self.tail_single_steps),
         }
 
 
@@ -137,6 +140,7 @@ EXPORTS = {
     "sp2_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                               C.POINTER(Info)]),
     "sp2_release_history": (C.c_int, [C.c_void_p]),
+    "sp2_synchronize": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "sp2_fermi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_double,
                             C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.POINTER(Opts),
                             C.c_void_p, C.c_void_p, C.POINTER(Info)]),

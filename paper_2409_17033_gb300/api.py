@@ -11,6 +11,7 @@ Functions (see include/sp2.h for the exact semantics):
   sp2_response(H, nocc, H1, ...)                Eq. DMPert (DM1)      -> (D1, D, info)
   sp2_susceptibility(H, nocc, A, direction=...) Eq. DMSuscept / DM2   -> (chi, D, info)
   sp2_adjoint(G, handle)                        Eq. DM2 on kept X_n   -> grad
+  synchronize(handle)                           sp2_synchronize       -> info of the last call
   sp2_fermi(H, mu, kT, B, ...)                  Sec. V.B finite T     -> (D1, D, info)
   sp2_scf_response(H, nocc, norb, K, Vext, ...) Eq. DM_CP_SCF         -> (q, residuals, iters, traj)
   mlp_forward / mlp_loss_grad / mlp_train       learned SCF preconditioner
@@ -25,7 +26,7 @@ import torch
 
 from . import _lib as L
 
-__all__ = ["Handle", "make_opts", "sp2_density", "sp2_response", "sp2_susceptibility",
+__all__ = ["Handle", "make_opts", "synchronize", "sp2_density", "sp2_response", "sp2_susceptibility",
            "sp2_adjoint", "sp2_fermi", "sp2_nonorth_susceptibility", "sp2_scf_response",
            "mlp_forward", "mlp_loss_grad",
            "mlp_train", "response_contract", "SP2Error"]
@@ -35,7 +36,8 @@ SP2Error = L.SP2Error
 
 def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: float = -1.0,
               max_iter: int = 0, min_iter: int = -1, sigma=None, bounds=None,
-              ckpt_k: int | str = 0, keep_history: bool = False, time_kernels: bool = False):
+              ckpt_k: int | str = 0, keep_history: bool = False, time_kernels: bool = False,
+              tail_f: float = 0.0):
     """sp2_opts with the library defaults for everything not given. Returns
     (opts, keepalive) where keepalive holds the branch array referenced by
     opts.sigma_in. ckpt_k="auto" selects SP2_CKPT_AUTO (keep as much of the
@@ -51,6 +53,7 @@ def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: flo
     o.ckpt_k = L.CKPT_AUTO if ckpt_k == "auto" else int(ckpt_k)
     o.keep_history = 1 if keep_history else 0
     o.time_kernels = 1 if time_kernels else 0
+    o.tail_f = float(tail_f)
     keep = None
     if sigma is not None:
         arr = (C.c_int8 * max(1, len(sigma)))(*[int(s) for s in sigma])
@@ -150,25 +153,49 @@ def default_handle() -> Handle:
     return h
 
 
+def _info_arg(sync: bool):
+    """The info struct of a call, or None for a call that returns without waiting
+    (complete it with synchronize(handle))."""
+    return L.Info() if sync else None
+
+
+def _info_ref(info):
+    return C.byref(info) if info is not None else None
+
+
+def _info_dict(info):
+    return info.to_dict() if info is not None else None
+
+
+def synchronize(handle: Handle | None = None, allow_noconv: bool = False) -> dict:
+    """sp2_synchronize: wait for the handle's stream, complete the last call made
+    with sync=False and return its info."""
+    h = handle or default_handle()
+    info = L.Info()
+    h.check(h.lib.sp2_synchronize(h.h, C.byref(info)), allow_noconv)
+    return info.to_dict()
+
+
 def sp2_density(H, nocc: float, mode="bf16x2", out=None, handle: Handle | None = None,
-                allow_noconv: bool = False, **kw):
+                allow_noconv: bool = False, sync: bool = True, **kw):
     """D = theta(mu I - H) by SP2 (Eq. DM0). H: (N, N) float64/float32, torch
-    CUDA tensor or numpy array. Returns (D, info dict)."""
+    CUDA tensor or numpy array. Returns (D, info dict); with sync=False (device
+    buffers) the call returns without waiting and info is None."""
     h = handle or default_handle()
     h.bind_stream()
     n = H.shape[0]
     D = out if out is not None else _empty_like(H, (n, n))
     opts, _keep = make_opts(mode, **kw)
-    info = L.Info()
+    info = _info_arg(sync)
     rc = h.lib.sp2_density(h.h, _ptr(H), n, _dtype_code(H), float(nocc), C.byref(opts), _ptr(D),
-                           C.byref(info))
+                           _info_ref(info))
     h.check(rc, allow_noconv)
-    return D, info.to_dict()
+    return D, _info_dict(info)
 
 
 def sp2_response(H, nocc: float, H1, diag_only: bool = False, mode="bf16x2",
                  want_density: bool = False, handle: Handle | None = None,
-                 allow_noconv: bool = False, **kw):
+                 allow_noconv: bool = False, sync: bool = True, **kw):
     """First-order responses D1_k to H1_k (Eq. DMPert). H1: (K, N, N), or
     (K, N) diagonals with diag_only=True. Returns (D1, D or None, info)."""
     h = handle or default_handle()
@@ -178,16 +205,17 @@ def sp2_response(H, nocc: float, H1, diag_only: bool = False, mode="bf16x2",
     D1 = _empty_like(H, (k, n, n))
     D = _empty_like(H, (n, n)) if want_density else None
     opts, _keep = make_opts(mode, **kw)
-    info = L.Info()
+    info = _info_arg(sync)
     rc = h.lib.sp2_response(h.h, _ptr(H), n, _dtype_code(H), float(nocc), _ptr(H1), k,
-                            1 if diag_only else 0, C.byref(opts), _ptr(D), _ptr(D1), C.byref(info))
+                            1 if diag_only else 0, C.byref(opts), _ptr(D), _ptr(D1),
+                            _info_ref(info))
     h.check(rc, allow_noconv)
-    return D1, D, info.to_dict()
+    return D1, D, _info_dict(info)
 
 
 def sp2_susceptibility(H, nocc: float, A, direction: str = "forward", diag_only: bool = False,
                        mode="bf16x2", want_density: bool = False, handle: Handle | None = None,
-                       allow_noconv: bool = False, out=None, D_out=None, **kw):
+                       allow_noconv: bool = False, out=None, D_out=None, sync: bool = True, **kw):
     """chi^A_l for observables A_l (L, N, N) or diagonals (L, N): forward
     Eq. DMSuscept, or backward Eq. DM2 with checkpointed X_n. Returns (chi, D or None, info).
     out / D_out: caller-owned result arrays (L, N, N) / (N, N) of H's dtype and kind,
@@ -201,13 +229,13 @@ def sp2_susceptibility(H, nocc: float, A, direction: str = "forward", diag_only:
     if tuple(chi.shape) != (l, n, n) or (D is not None and tuple(D.shape) != (n, n)):
         raise ValueError("out / D_out have the wrong shape")
     opts, _keep = make_opts(mode, **kw)
-    info = L.Info()
+    info = _info_arg(sync)
     d = {"forward": 0, "backward": 1}[direction]
     rc = h.lib.sp2_susceptibility(h.h, _ptr(H), n, _dtype_code(H), float(nocc), _ptr(A), l,
                                   1 if diag_only else 0, d, C.byref(opts), _ptr(D), _ptr(chi),
-                                  C.byref(info))
+                                  _info_ref(info))
     h.check(rc, allow_noconv)
-    return chi, D, info.to_dict()
+    return chi, D, _info_dict(info)
 
 
 def sp2_nonorth_susceptibility(H, S, nocc: float, A, mode="fp64", want_z: bool = False,
@@ -229,15 +257,15 @@ def sp2_nonorth_susceptibility(H, S, nocc: float, A, mode="fp64", want_z: bool =
     return D, WH, WS, Z, info.to_dict()
 
 
-def sp2_adjoint(G, handle: Handle):
+def sp2_adjoint(G, handle: Handle, sync: bool = True):
     """Eq. DM2 for the symmetric part of G against the X_n history kept by the
     handle's last sp2_density(keep_history=True). Returns d Tr[G D]/dH."""
     h = handle
     h.bind_stream()
     n = G.shape[0]
     out = _empty_like(G, (n, n))
-    info = L.Info()
-    rc = h.lib.sp2_adjoint(h.h, _ptr(G), n, _dtype_code(G), _ptr(out), C.byref(info))
+    info = _info_arg(sync)
+    rc = h.lib.sp2_adjoint(h.h, _ptr(G), n, _dtype_code(G), _ptr(out), _info_ref(info))
     h.check(rc)
     return out
 

@@ -294,6 +294,7 @@ struct KParams {
   float* zmax;             // FP16X2 EPI_PLAIN: per batch entry, receives max |C|
   unsigned long long wait_ns;
   int withhold;            // test hook: CTA 0 never issues its first load
+  int tail;                // split-tail mode: st->plane1[step] selects the hi planes alone
 };
 
 // Tensor maps of one launch: the left factor's planes with 128-row boxes (A role)
@@ -482,7 +483,11 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* abortf = &st->abort_flag;
-  const int total_kb = p.nseg * p.nkb;
+  // segments of this launch: the split product, or in the split-tail mode's bulk
+  // steps the hi planes alone (one segment; two for the symmetric response)
+  const int nbase = (p.tail && st->plane1[p.step]) ? 1 : p.nbase;
+  const int nseg = EPI == EPI_SYMM ? 2 * nbase : nbase;
+  const int total_kb = nseg * p.nkb;
   const int nchunks = total_kb / p.ch;
   // persistent static schedule: this CTA handles tiles blockIdx.x, +gridDim.x, ...
   const int my_tiles =
@@ -534,9 +539,9 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
           if (p.withhold && blockIdx.x == 0 && g == 0) continue;  // test hook: never completes
           const int seg = kb / nkb;
           const int kx = (kb - seg * nkb) * BK;
-          const bool swap = EPI == EPI_SYMM && seg >= p.nbase;   // second half: [Q | .] . [. ; P]
+          const bool swap = EPI == EPI_SYMM && seg >= nbase;   // second half: [Q | .] . [. ; P]
           int pa, pb;
-          seg_planes<KIND>(swap ? seg - p.nbase : seg, pa, pb);
+          seg_planes<KIND>(swap ? seg - nbase : seg, pa, pb);
           const CUtensorMap* ma = swap ? &maps.qa[pa] : &maps.pa[pa];
           const CUtensorMap* mb = swap ? &maps.pb[pb] : &maps.qb[pb];
           const int arow = swap ? t.row0 - bat * (int)np : t.row0;
@@ -644,7 +649,7 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
                        "r"((uint32_t)(TCOLS * sizeof(float)))
                        : "memory");
         float wgt = 1.0f;
-        if constexpr (F16) wgt = (((c * p.ch) / p.nkb) % p.nbase) == 0 ? 1.0f : 1.0f / kLoScale;
+        if constexpr (F16) wgt = (((c * p.ch) / p.nkb) % nbase) == 0 ? 1.0f : 1.0f / kLoScale;
 #pragma unroll
         for (int c0 = 0; c0 < TCOLS; c0 += 16) {
           uint32_t v[16];
@@ -820,6 +825,7 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   p.zmax = f16 ? L.zmax : nullptr;
   p.wait_ns = L.tune.wait_ns;
   p.withhold = L.tune.withhold;
+  p.tail = L.tail;
   // persistent: one CTA per SM (the shared-memory ring allows no second one)
   const int grid = tc_grid(L.ntiles);
   if (kind == KIND_FP16X2) return launch_epi<KIND_FP16X2>(L.epi, maps, p, grid, s);

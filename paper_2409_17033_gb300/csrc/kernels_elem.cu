@@ -81,6 +81,28 @@ __global__ void k_bounds(const void* H, int64_t n, int dtype, double2* part) {
   if (threadIdx.x == 0) part[blockIdx.x] = mm;
 }
 
+// Sec. II: X_1 = alpha I + beta H maps [eps_min, eps_max] onto [1, 0] in reverse
+// order, alpha = eps_max / (eps_max - eps_min), beta = -1 / (eps_max - eps_min); a
+// point spectrum is widened to [eps - 1/2, eps + 1/2].
+__device__ void set_coefficients(DevState* st, double lo, double hi) {
+  if (!isfinite(lo) || !isfinite(hi)) {
+    st->bounds[0] = lo;
+    st->bounds[1] = hi;
+    st->nonfinite = 1;
+    st->stop_at = -1;   // every step kernel is a no-op
+    return;
+  }
+  if (!(hi > lo)) {
+    lo -= 0.5;
+    hi += 0.5;
+  }
+  st->bounds[0] = lo;
+  st->bounds[1] = hi;
+  const double w = hi - lo;
+  st->alpha = hi / w;
+  st->beta = -1.0 / w;
+}
+
 __global__ void k_bounds_final(const double2* part, int nparts, DevState* st) {
   double lo = INFINITY, hi = -INFINITY;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -88,7 +110,25 @@ __global__ void k_bounds_final(const double2* part, int nparts, DevState* st) {
     hi = nmax(hi, part[i].y);
   }
   double2 mm = block_minmax(lo, hi);
-  if (threadIdx.x == 0) { st->bounds[0] = mm.x; st->bounds[1] = mm.y; }
+  if (threadIdx.x == 0) set_coefficients(st, mm.x, mm.y);
+}
+
+__global__ void k_set_bounds(DevState* st, double lo, double hi) { set_coefficients(st, lo, hi); }
+
+struct SigmaArg {
+  int8_t s[SP2_MAX_ITER];
+};
+
+__global__ void k_set_sigma(DevState* st, SigmaArg a, int m) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) st->sigma[i + 1] = a.s[i];
+}
+
+// an adjoint recursion runs every step it is given and keeps no floor candidate
+__global__ void k_adjoint_state(DevState* st) {
+  st->stop_at = 0;
+  st->keep_step = 0;
+  st->abort_flag = 0;
+  st->nonfinite = 0;
 }
 
 // ------------------------------------------------------------ init
@@ -131,7 +171,14 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
 
 __global__ void k_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
                        int diag_only, int symmetrize, double alpha, double beta, int mode,
-                       MatBuf dst, Part3* part, float* ymax) {
+                       MatBuf dst, Part3* part, float* ymax, int coef, const DevState* st) {
+  if (coef == INIT_STATE) {
+    alpha = st->alpha;
+    beta = st->beta;
+  } else if (coef == INIT_STATE_BETA) {
+    alpha = 0.0;
+    beta = st->beta;
+  }
   double t1 = 0.0, t2 = 0.0;
   const bool planes = !(mode == SP2_MODE_FP16X2 && ymax != nullptr);
   const int64_t rows = batch * np;
@@ -189,6 +236,11 @@ __global__ void k_decide(const Part3* part, DevState* st, DecideParams p) {
   st->t1[n] = t1;
   st->t2[n] = t2;
   if (n >= 2) st->f[n - 1] = f;  // the step that produced X_n measured X_{n-1}
+  // split-tail mode: step n (X_n -> X_{n+1}) uses single-plane products while the
+  // idempotency error of the last measured iterate exceeds tail_f; once a step
+  // has used split products, every later one does
+  if (p.tail_f > 0.0)
+    st->plane1[n] = n == 1 ? 1 : (st->plane1[n - 1] && st->f[n - 1] > p.tail_f ? 1 : 0);
   if (!isfinite(t1) || !isfinite(t2)) {
     st->nonfinite = 1;
     st->stop_at = (n - 1 >= 1) ? n - 1 : -1;
@@ -397,7 +449,8 @@ __global__ void __launch_bounds__(kSymThreads)
 
 // ------------------------------------------------------------ output copy
 __global__ void k_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
-                           double scale, void* dst, int dtype) {
+                           double scale, void* dst, int dtype, const DevState* beta_state) {
+  if (beta_state) scale *= beta_state->beta;
   const int64_t total = batch * n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -621,10 +674,29 @@ int init_nparts(int64_t np) { return (int)(np < 1024 ? np : 1024); }
 
 cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
                         int diag_only, int symmetrize, double alpha, double beta, int mode,
-                        MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s) {
+                        MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s,
+                        int coef, const DevState* st) {
   int grid = part ? nparts : grid_for(batch * np, 1, 4096);
   k_init<<<grid, kRedThreads, 0, s>>>(src, n, np, batch, dtype, diag_only, symmetrize, alpha,
-                                      beta, mode, dst, part, ymax);
+                                      beta, mode, dst, part, ymax, coef, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_bounds(DevState* st, double eps_min, double eps_max, cudaStream_t s) {
+  k_set_bounds<<<1, 1, 0, s>>>(st, eps_min, eps_max);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_sigma(DevState* st, const int8_t* sigma, int m, cudaStream_t s) {
+  if (m < 0 || m > SP2_MAX_ITER) return cudaErrorInvalidValue;
+  SigmaArg a;
+  for (int i = 0; i < SP2_MAX_ITER; ++i) a.s[i] = i < m ? sigma[i] : 0;
+  k_set_sigma<<<1, 256, 0, s>>>(st, a, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_state(DevState* st, cudaStream_t s) {
+  k_adjoint_state<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();
 }
 
@@ -670,9 +742,10 @@ cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t
 }
 
 cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
-                            double scale, void* dst, int dtype, cudaStream_t s) {
+                            double scale, void* dst, int dtype, cudaStream_t s,
+                            const DevState* beta_state) {
   k_copy_out<<<grid_for(batch * n * n, 256, 8192), 256, 0, s>>>(src, n, np, batch, mode, scale,
-                                                                 dst, dtype);
+                                                                 dst, dtype, beta_state);
   return cudaGetLastError();
 }
 

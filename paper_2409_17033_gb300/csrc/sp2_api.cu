@@ -35,6 +35,17 @@ struct sp2_handle_s {
   DevState* d_state = nullptr;
   DevState* h_state = nullptr;  // pinned mirror
   TcTuning tune;                // product-kernel launch settings (sp2_set_option)
+  // The step loop reads the trailing part of the device state after every step
+  // into a pinned ring (kRing slots), each followed by an event; the host waits
+  // only for the step kLookahead behind the one it enqueues, so the GPU never
+  // idles and at most kLookahead no-op steps follow the stop.
+  static constexpr int kRing = 16, kLookahead = 8;
+  DevState* ring = nullptr;     // pinned, kRing snapshots (tail only)
+  cudaEvent_t ring_ev[kRing] = {};
+  // side stream for host copies that overlap later work of the same call
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_ev[2] = {};
+  bool side_pending = false;
   std::vector<cudaEvent_t> events;  // pool for time_kernels (start/stop pairs)
 
   // X_n history kept for sp2_adjoint
@@ -42,9 +53,14 @@ struct sp2_handle_s {
     bool valid = false;
     int64_t n = 0, np = 0;
     int mode = 0, M = 0, k = 4;
+    int tail = 0;            // split-tail mode of the kept recursion
     double beta = 0.0;
-    std::vector<int> sigma;  // sigma[1..M]
+    std::vector<int> sigma;  // sigma[1..M] (filled when the producing call completes)
   } hist;
+
+  // the work of the last call that has not been waited for (sp2_synchronize)
+  struct Pending;
+  Pending* pending = nullptr;
 };
 
 namespace {
@@ -192,6 +208,31 @@ int finish_out(sp2_handle_t h, const OutStage& o) {
   return SP2_OK;
 }
 
+// The host copy of an output that is final while later work of the call still
+// runs: on the handle's side stream, after what the main stream has enqueued so
+// far; join_beside makes the main stream wait for it.
+int finish_out_beside(sp2_handle_t h, const OutStage& o) {
+  if (!o.host) return SP2_OK;
+  if (!h->side) {
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->side_ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->side_ev[1], cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(h->side_ev[0], h->stream));
+  CK(cudaStreamWaitEvent(h->side, h->side_ev[0], 0));
+  CK(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, h->side));
+  CK(cudaEventRecord(h->side_ev[1], h->side));
+  h->side_pending = true;
+  return SP2_OK;
+}
+
+int join_beside(sp2_handle_t h) {
+  if (!h->side_pending) return SP2_OK;
+  CK(cudaStreamWaitEvent(h->stream, h->side_ev[1], 0));
+  h->side_pending = false;
+  return SP2_OK;
+}
+
 size_t dsize(int dtype) { return dtype == SP2_F64 ? 8 : 4; }
 
 // --------------------------------------------------------------- tile lists
@@ -250,6 +291,7 @@ struct Ctx {
   double alg = 0.0;       // algorithmic product flops
   int64_t kernels = 0;    // every kernel launched
   bool timing = false;
+  int tail = 0;           // split-tail mode (product kernels read st->plane1)
   std::vector<std::pair<int, int>> timed;  // (step, event-pair index) per timed product launch
 };
 
@@ -298,6 +340,7 @@ int tc_common(Ctx& c, TcLaunch* L, int ntiles) {
   L->part = c.part;
   L->ntiles = ntiles;
   L->tune = c.h->tune;
+  L->tail = c.tail;
   return SP2_OK;
 }
 
@@ -503,6 +546,7 @@ int validate_opts(sp2_handle_t h, const sp2_opts* o) {
         return fail(h, SP2_EINVAL, "sigma_in[%d] = %d is not +-1", i, (int)o->sigma_in[i]);
   if (o->ckpt_k < 1 && o->ckpt_k != SP2_CKPT_AUTO)
     return fail(h, SP2_EINVAL, "ckpt_k must be >= 1 or SP2_CKPT_AUTO");
+  if (!(o->tail_f >= 0.0)) return fail(h, SP2_EINVAL, "tail_f must be >= 0");
   return SP2_OK;
 }
 
@@ -535,6 +579,25 @@ int poll_state(sp2_handle_t h) {
   return SP2_OK;
 }
 
+// enqueue a snapshot of the state's trailing part into ring slot `step` % kRing
+int ring_record(sp2_handle_t h, int step) {
+  const int slot = step % sp2_handle_s::kRing;
+  const size_t off = devstate_tail_offset();
+  CK(cudaMemcpyAsync(reinterpret_cast<char*>(h->ring + slot) + off,
+                     reinterpret_cast<const char*>(h->d_state) + off, sizeof(DevState) - off,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaEventRecord(h->ring_ev[slot], h->stream));
+  return SP2_OK;
+}
+
+// wait for the snapshot of `step` and return it
+int ring_read(sp2_handle_t h, int step, const DevState** out) {
+  const int slot = step % sp2_handle_s::kRing;
+  CK(cudaEventSynchronize(h->ring_ev[slot]));
+  *out = h->ring + slot;
+  return SP2_OK;
+}
+
 // --------------------------------------------------------------- the SP2 driver
 struct Sp2Out {
   int M = 0;
@@ -549,49 +612,38 @@ struct Sp2Out {
 // response Y of Eq. DMPert / DMSuscept is carried along (merged form,
 // Appendix), starting from Y_1 = beta B. If keep, X_n is checkpointed every
 // ckpt_k steps for the adjoint.
+// The spectral bounds, alpha and beta are computed on the device; the host
+// enqueues step after step and learns of the stop from the snapshot ring, at
+// most kLookahead steps behind, so it never waits for the GPU to drain. On return
+// the stop (M, the kept iterate) is known; the GPU may still be running the last
+// steps (no-ops past the stop).
 int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, const sp2_opts& o,
             const void* Bd, int64_t ybatch, int b_diag, bool keep, MatBuf X[2], MatBuf Y[2],
             Ctx& c, Sp2Out* out) {
   const int64_t np = pad_n(n);
   const int mode = o.mode;
-  // spectral bounds (Sec. II)
-  double emin = o.eps_min, emax = o.eps_max;
   CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));
-  if (!(emin < emax)) {
+  // spectral bounds (Sec. II) and X_1 = alpha I + beta H, on the device
+  if (o.eps_min < o.eps_max) {
+    CK(launch_set_bounds(h->d_state, o.eps_min, o.eps_max, h->stream));
+    c.kernels++;
+  } else {
     const int nb = bounds_nparts(n);
     void* bp;
     TRY(ws(h, "bounds.part", nb * sizeof(double2), &bp));
     CK(launch_bounds(Hd, n, dtype, static_cast<double2*>(bp), nb, h->d_state, h->stream));
     c.kernels += 2;
-    TRY(poll_state(h));
-    emin = h->h_state->bounds[0];
-    emax = h->h_state->bounds[1];
-    if (!std::isfinite(emin) || !std::isfinite(emax))
-      return fail(h, SP2_ENONFINITE, "non-finite spectral bounds (NaN/Inf in H)");
   }
-  if (!(emax > emin)) {  // point spectrum: any interval around it maps into [0, 1]
-    emin -= 0.5;
-    emax += 0.5;
-  }
-  const double w = emax - emin;
-  const double alpha = emax / w, beta = -1.0 / w;
-  out->alpha = alpha;
-  out->beta = beta;
-  out->emin = emin;
-  out->emax = emax;
-
   if (o.fixed_m > 0) {
-    for (int i = 0; i < o.fixed_m; ++i) h->h_state->sigma[i + 1] = o.sigma_in[i];
-    CK(cudaMemcpyAsync(h->d_state->sigma, h->h_state->sigma, sizeof(int) * (o.fixed_m + 2),
-                       cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));  // h_state is reused by later polls
+    CK(launch_set_sigma(h->d_state, o.sigma_in, o.fixed_m, h->stream));
+    c.kernels++;
   }
 
   TRY(mat(h, "X0", np, np, mode, &X[0]));
   TRY(mat(h, "X1", np, np, mode, &X[1]));
   const int ni = init_nparts(np);
-  CK(launch_init(Hd, n, np, 1, dtype, 0, 0, alpha, beta, mode, X[1], c.part, ni, nullptr,
-                 h->stream));
+  CK(launch_init(Hd, n, np, 1, dtype, 0, 0, 0.0, 0.0, mode, X[1], c.part, ni, nullptr, h->stream,
+                 INIT_STATE, h->d_state));
   c.kernels++;
   DecideParams dp;
   dp.nocc = nocc;
@@ -600,6 +652,8 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   dp.min_iter = o.min_iter;
   dp.max_iter = o.max_iter;
   dp.fixed_m = o.fixed_m;
+  dp.tail_f = split_mode(mode) ? o.tail_f : 0.0;
+  c.tail = dp.tail_f > 0.0 ? 1 : 0;
   dp.n = 1;
   dp.nparts = ni;
   CK(launch_decide(c.part, c.st, dp, h->stream));
@@ -613,8 +667,8 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
       TRY(scales(h, "Y.scale", ybatch, &sc));
       CK(cudaMemsetAsync(sc.ymax, 0, sizeof(float) * 2 * ybatch, h->stream));
     }
-    CK(launch_init(Bd, n, np, ybatch, dtype, b_diag, 0, 0.0, beta, mode, Y[1], nullptr, 0,
-                   f16 ? sc.ymax + 1 * ybatch : nullptr, h->stream));
+    CK(launch_init(Bd, n, np, ybatch, dtype, b_diag, 0, 0.0, 0.0, mode, Y[1], nullptr, 0,
+                   f16 ? sc.ymax + 1 * ybatch : nullptr, h->stream, INIT_STATE_BETA, h->d_state));
     c.kernels++;
     if (f16) {
       CK(launch_split_scaled(Y[1], np, sc, 1, h->stream));
@@ -624,10 +678,7 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   }
 
   const int maxit = o.fixed_m > 0 ? o.fixed_m : o.max_iter;
-  const int chunk = np <= 1024 ? 8 : (np <= 4096 ? 2 : 1);
   const size_t xbytes = (size_t)np * np * master_size(mode);
-  int M = 0;
-  bool stopped = false;
   const double f0 = c.flops, a0 = c.alg;
   const int64_t l0 = c.launches;
   double fstep = 0.0, astep = 0.0;
@@ -639,7 +690,9 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
     TRY(ws(h, "Xbest.m", xbytes, &xbest.master));
     if (ybatch > 0) TRY(ws(h, "Ybest.m", (size_t)ybatch * xbytes, &ybest.master));
   }
-  for (int step = 1; step <= maxit && !stopped; ++step) {
+  const DevState* seen = nullptr;   // latest snapshot read
+  int last = 0;                     // last step enqueued
+  for (int step = 1; step <= maxit; ++step) {
     const MatBuf& xin = X[step % 2];
     const MatBuf& xo = X[(step + 1) % 2];
     if (keep && (step - 1) % o.ckpt_k == 0) {
@@ -678,23 +731,32 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
       astep = c.alg - a0;
       lstep = c.launches - l0;
     }
-    if (step % chunk == 0 || step == maxit) {
-      TRY(poll_state(h));
-      const DevState& s = *h->h_state;
-      if (s.nonfinite) return fail(h, SP2_ENONFINITE, "non-finite trace at step %d", step);
-      if (s.stop_at != 0) {
-        M = s.stop_at;
-        stopped = true;
-      }
+    TRY(ring_record(h, step));
+    last = step;
+    if (step > sp2_handle_s::kLookahead) {
+      TRY(ring_read(h, step - sp2_handle_s::kLookahead, &seen));
+      if (seen->stop_at != 0 || seen->abort_flag) break;
     }
   }
-  if (!stopped) M = maxit;
+  if (!seen || (seen->stop_at == 0 && !seen->abort_flag)) TRY(ring_read(h, last, &seen));
+  const DevState& S = *seen;
+  out->alpha = S.alpha;
+  out->beta = S.beta;
+  out->emin = S.bounds[0];
+  out->emax = S.bounds[1];
+  if (S.abort_flag) return fail(h, SP2_ETIMEOUT, "a device-side wait timed out in a product kernel");
+  if (S.nonfinite) {
+    if (S.stop_at < 0) return fail(h, SP2_ENONFINITE, "non-finite spectral bounds (NaN/Inf in H)");
+    return fail(h, SP2_ENONFINITE, "non-finite trace after step %d", S.stop_at);
+  }
+  const bool stopped = S.stop_at > 0;
+  const int M = stopped ? S.stop_at : maxit;
   out->M = M;
   out->converged = stopped;
-  const bool back = stopped && h->h_state->backtracked;
+  const bool back = stopped && S.backtracked;
   out->xout = back ? xbest : X[(M + 1) % 2];
   out->yout = back ? ybest : Y[(M + 1) % 2];
-  out->stop_step = stopped ? h->h_state->stop_step : M;
+  out->stop_step = stopped ? S.stop_step : M;
   if (out->stop_step < M) out->stop_step = M;
   // executed-work accounting covers only the steps that ran (later launches were no-ops)
   c.flops = f0 + fstep * out->stop_step;
@@ -718,6 +780,7 @@ void fill_info(sp2_handle_t h, const Sp2Out& r, const Ctx& c, sp2_info* info) {
   for (int i = 1; i <= r.M; ++i) info->idem_fro[i - 1] = s.f[i];
   info->trace = s.t1[r.M + 1];
   info->idem_err = s.t1[r.M + 1] - s.t2[r.M + 1];
+  for (int i = 1; i <= r.M; ++i) info->tail_single_steps += s.plane1[i] ? 1 : 0;
   info->n_gemm_launches = c.launches;
   info->executed_flops = c.flops;
   info->algorithmic_flops = c.alg;
@@ -758,19 +821,23 @@ int make_ctx(sp2_handle_t h, int mode, int64_t n, int64_t np, bool timing, Ctx* 
 // n = M..1; result beta * G_1. X_n is restored from the checkpoint of its
 // segment and the segment is recomputed forward with the stored branches.
 int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int symmetrize,
-                int dtype, void* outd, int out_dtype, Ctx& c) {
+                int dtype, void* outd, int out_dtype, Ctx& c, DevState** adj_state) {
   auto& hs = h->hist;
   const int64_t np = hs.np, n = hs.n;
   const int mode = hs.mode, M = hs.M, k = hs.k;
-  // branch signs for the step kernels; no stop
+  // the adjoint's own state: the branch signs of the kept forward recursion (a
+  // device copy), with nothing to stop and no floor candidate to keep
   void* stp;
+  void* hst;
   TRY(ws(h, "adj.state", sizeof(DevState), &stp));
+  TRY(ws(h, "hist.state", sizeof(DevState), &hst));
   DevState* ast = static_cast<DevState*>(stp);
-  memset(h->h_state, 0, sizeof(DevState));
-  for (int i = 1; i <= M; ++i) h->h_state->sigma[i] = hs.sigma[i];
-  CK(cudaMemcpyAsync(ast, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(ast, hst, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
+  CK(launch_adjoint_state(ast, h->stream));
+  c.kernels++;
   c.st = ast;
+  c.tail = hs.tail;   // the adjoint step n uses the planes its forward step n used
+  *adj_state = ast;
 
   MatBuf G[2];
   TRY(mat(h, "G0", batch * np, np, mode, &G[0]));
@@ -837,15 +904,117 @@ int run_adjoint(sp2_handle_t h, const void* Bd, int64_t batch, int b_diag, int s
   CK(launch_copy_out(G[gs], n, np, batch, mode, hs.beta, outd, out_dtype, h->stream));
   c.kernels++;
   c.st = h->d_state;
-  // the adjoint's product launches report a timed-out device wait in their own state
-  CK(cudaMemcpyAsync(&h->h_state->abort_flag, &ast->abort_flag, sizeof(int),
-                     cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  if (h->h_state->abort_flag)
-    return fail(h, SP2_ETIMEOUT, "a device-side wait timed out in a product kernel (adjoint)");
+  // a timed-out device wait of the adjoint's launches shows in its own state,
+  // which the completion of the call reads
   return SP2_OK;
 }
 
+// keep the forward recursion's device state (branch signs) for a later adjoint
+int keep_history(sp2_handle_t h, const Sp2Out& r, int64_t n, int64_t np, int mode, int k,
+                 int tail) {
+  void* hst;
+  TRY(ws(h, "hist.state", sizeof(DevState), &hst));
+  CK(cudaMemcpyAsync(hst, h->d_state, sizeof(DevState), cudaMemcpyDeviceToDevice, h->stream));
+  auto& hs = h->hist;
+  hs.valid = true;
+  hs.n = n;
+  hs.np = np;
+  hs.mode = mode;
+  hs.M = r.M;
+  hs.k = k;
+  hs.beta = r.beta;
+  hs.tail = tail;
+  hs.sigma.clear();   // filled when the call completes
+  return SP2_OK;
+}
+
+
+// --------------------------------------------------------------- call completion
+}  // namespace
+
+// What a call left for its completion: the device state to read, the status
+// known when it returned, and what its info reports.
+struct sp2_handle_s::Pending {
+  bool sp2 = false;               // a forward recursion ran: info from the device state
+  bool adjoint = false;           // sp2_adjoint: info from the kept history
+  Sp2Out r;
+  Ctx c;
+  int ckpt_k = 0;
+  bool hist_sigma = false;        // fill the kept history's branch signs
+  DevState* adj_state = nullptr;  // an adjoint ran: its abort flag
+  int status = SP2_OK;            // known when the call returned (ENOCONV)
+  std::string msg;
+};
+
+namespace {
+
+void drop_pending(sp2_handle_t h) {
+  delete h->pending;
+  h->pending = nullptr;
+}
+
+// Waits for the handle's stream, reads the device state and completes the last
+// call: its status (a timed-out wait of the adjoint shows only now) and its info.
+int complete_pending(sp2_handle_t h, sp2_info* info) {
+  sp2_handle_s::Pending* p = h->pending;
+  h->pending = nullptr;
+  CK(cudaStreamSynchronize(h->stream));
+  if (!p) {
+    if (info) memset(info, 0, sizeof *info);
+    return SP2_OK;
+  }
+  int code = p->status;
+  std::string msg = p->msg;
+  cudaError_t e = cudaMemcpy(h->h_state, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost);
+  int adj_abort = 0;
+  if (e == cudaSuccess && p->adj_state)
+    e = cudaMemcpy(&adj_abort, &p->adj_state->abort_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(h, SP2_ECUDA, "reading the device state failed: %s", cudaGetErrorString(e));
+  }
+  if (adj_abort || (p->sp2 && h->h_state->abort_flag)) {
+    code = SP2_ETIMEOUT;
+    msg = "a device-side wait timed out in a product kernel";
+  }
+  auto& hs = h->hist;
+  if (p->hist_sigma && hs.valid) {
+    hs.sigma.assign(hs.M + 1, 0);
+    for (int i = 1; i <= hs.M; ++i) hs.sigma[i] = h->h_state->sigma[i];
+  }
+  if (info) {
+    if (p->sp2) {
+      fill_info(h, p->r, p->c, info);
+    } else {
+      memset(info, 0, sizeof *info);
+      if (p->adjoint) {
+        info->M = hs.M;
+        info->converged = 1;
+        info->beta = hs.beta;
+        void* hst;
+        if (ws(h, "hist.state", sizeof(DevState), &hst) == SP2_OK &&
+            cudaMemcpy(h->h_state, hst, sizeof(DevState), cudaMemcpyDeviceToHost) == cudaSuccess)
+          for (int i = 1; i <= hs.M; ++i) info->sigma[i - 1] = (int8_t)h->h_state->sigma[i];
+      }
+    }
+    fill_timing(p->c, p->adjoint ? hs.M : p->r.M, info);
+    info->ckpt_k = p->ckpt_k;
+  }
+  delete p;
+  if (code != SP2_OK) return fail(h, code, "%s", msg.c_str());
+  return SP2_OK;
+}
+
+// Ends a call whose work is enqueued: it completes now when the caller wants info
+// or gets results in host memory, else it returns at once and sp2_synchronize
+// completes it.
+int finish_call(sp2_handle_t h, sp2_handle_s::Pending* p, sp2_info* info, bool wait) {
+  drop_pending(h);
+  h->pending = p;
+  if (wait || info) return complete_pending(h, info);
+  if (p->status != SP2_OK) return fail(h, p->status, "%s", p->msg.c_str());
+  return SP2_OK;
+}
 
 // --------------------------------------------------------------- finite temperature
 // A padded matrix of the finite-temperature recursion with its plane scale
@@ -993,12 +1162,27 @@ int sp2_create(sp2_handle_t* out, void* stream, size_t limit) {
     cudaGetLastError();
     code = SP2_ECUDA;
   }
+  if (code == SP2_OK &&
+      cudaMallocHost(&h->ring, sizeof(DevState) * sp2_handle_s::kRing) != cudaSuccess) {
+    cudaGetLastError();
+    code = SP2_ECUDA;
+  }
+  for (int i = 0; code == SP2_OK && i < sp2_handle_s::kRing; ++i)
+    if (cudaEventCreateWithFlags(&h->ring_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      code = SP2_ECUDA;
+    }
   if (code != SP2_OK) {
+    for (int i = 0; i < sp2_handle_s::kRing; ++i)
+      if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
+    if (h->ring) cudaFreeHost(h->ring);
+    if (h->h_state) cudaFreeHost(h->h_state);
     if (h->d_state) cudaFree(h->d_state);
     delete h;
     return code;
   }
   memset(h->h_state, 0, sizeof(DevState));
+  memset(h->ring, 0, sizeof(DevState) * sp2_handle_s::kRing);
   *out = h;
   return SP2_OK;
 }
@@ -1011,8 +1195,24 @@ int sp2_destroy(sp2_handle_t h) {
   for (auto& kv : h->tiles) cudaFree(kv.second.d);
   if (h->d_state) cudaFree(h->d_state);
   if (h->h_state) cudaFreeHost(h->h_state);
+  for (int i = 0; i < sp2_handle_s::kRing; ++i)
+    if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
+  if (h->ring) cudaFreeHost(h->ring);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+    cudaEventDestroy(h->side_ev[0]);
+    cudaEventDestroy(h->side_ev[1]);
+  }
+  for (auto e : h->events) cudaEventDestroy(e);
+  delete h->pending;
   delete h;
   return SP2_OK;
+}
+
+int sp2_synchronize(sp2_handle_t h, sp2_info* info) {
+  if (!h) return SP2_EINVAL;
+  return complete_pending(h, info);
 }
 
 int sp2_set_stream(sp2_handle_t h, void* stream) {
@@ -1074,24 +1274,18 @@ int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc
   CK(launch_copy_out(r.xout, N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
   c.kernels++;
   TRY(finish_out(h, od));
-  CK(cudaStreamSynchronize(h->stream));
-  fill_info(h, r, c, info);
-  fill_timing(c, r.M, info);
-  if (keep) {
-    auto& hs = h->hist;
-    hs.valid = true;
-    hs.n = N;
-    hs.np = np;
-    hs.mode = o.mode;
-    hs.M = r.M;
-    hs.k = o.ckpt_k;
-    hs.beta = r.beta;
-    hs.sigma.assign(r.M + 1, 0);
-    for (int i = 1; i <= r.M; ++i) hs.sigma[i] = h->h_state->sigma[i];
-    if (info) info->ckpt_k = o.ckpt_k;
+  if (keep) TRY(keep_history(h, r, N, np, o.mode, o.ckpt_k, c.tail));
+  auto* p = new sp2_handle_s::Pending();
+  p->sp2 = true;
+  p->r = r;
+  p->c = c;
+  p->ckpt_k = keep ? o.ckpt_k : 0;
+  p->hist_sigma = keep;
+  if (!r.converged) {
+    p->status = SP2_ENOCONV;
+    p->msg = "no convergence in " + std::to_string(r.M) + " steps";
   }
-  if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
-  return SP2_OK;
+  return finish_call(h, p, info, od.host);
 }
 
 int sp2_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc, const void* H1,
@@ -1131,11 +1325,15 @@ int sp2_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double noc
     c.kernels++;
     TRY(finish_out(h, oy));
   }
-  CK(cudaStreamSynchronize(h->stream));
-  fill_info(h, r, c, info);
-  fill_timing(c, r.M, info);
-  if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
-  return SP2_OK;
+  auto* p = new sp2_handle_s::Pending();
+  p->sp2 = true;
+  p->r = r;
+  p->c = c;
+  if (!r.converged) {
+    p->status = SP2_ENOCONV;
+    p->msg = "no convergence in " + std::to_string(r.M) + " steps";
+  }
+  return finish_call(h, p, info, (D && od.host) || (K > 0 && oy.host));
 }
 
 int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad, sp2_info* info);
@@ -1176,29 +1374,26 @@ int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, doub
   if (D) {
     CK(launch_copy_out(r.xout, N, np, 1, o.mode, 1.0, od.dev, dtype, h->stream));
     c.kernels++;
-    TRY(finish_out(h, od));
+    // D is final before the adjoint starts: a host copy of it runs beside the adjoint
+    TRY(finish_out_beside(h, od));
   }
-  CK(cudaStreamSynchronize(h->stream));
-  fill_info(h, r, c, info);
-  auto& hs = h->hist;
-  hs.valid = true;
-  hs.n = N;
-  hs.np = np;
-  hs.mode = o.mode;
-  hs.M = r.M;
-  hs.k = o.ckpt_k;
-  hs.beta = r.beta;
-  hs.sigma.assign(r.M + 1, 0);
-  for (int i = 1; i <= r.M; ++i) hs.sigma[i] = h->h_state->sigma[i];
+  TRY(keep_history(h, r, N, np, o.mode, o.ckpt_k, c.tail));
+  auto* p = new sp2_handle_s::Pending();
   if (L > 0) {
-    TRY(run_adjoint(h, Bd, L, a_diag_only, 0, dtype, oy.dev, dtype, c));
+    TRY(run_adjoint(h, Bd, L, a_diag_only, 0, dtype, oy.dev, dtype, c, &p->adj_state));
     TRY(finish_out(h, oy));
   }
-  CK(cudaStreamSynchronize(h->stream));
-  fill_timing(c, r.M, info);
-  if (info) info->ckpt_k = o.ckpt_k;
-  if (!r.converged) return fail(h, SP2_ENOCONV, "no convergence in %d steps", r.M);
-  return SP2_OK;
+  TRY(join_beside(h));
+  p->sp2 = true;
+  p->r = r;
+  p->c = c;
+  p->ckpt_k = o.ckpt_k;
+  p->hist_sigma = true;
+  if (!r.converged) {
+    p->status = SP2_ENOCONV;
+    p->msg = "no convergence in " + std::to_string(r.M) + " steps";
+  }
+  return finish_call(h, p, info, (D && od.host) || (L > 0 && oy.host));
 }
 
 int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad, sp2_info* info) {
@@ -1216,18 +1411,16 @@ int sp2_adjoint(sp2_handle_t h, const void* G, int64_t N, int dtype, void* grad,
   TRY(stage_out(h, "Y", grad, mb, &oy));
   Ctx c;
   TRY(make_ctx(h, h->hist.mode, h->hist.n, h->hist.np, true, &c));
-  TRY(run_adjoint(h, Gd, 1, 0, 1, dtype, oy.dev, dtype, c));
-  TRY(finish_out(h, oy));
-  CK(cudaStreamSynchronize(h->stream));
-  if (info) {
-    memset(info, 0, sizeof *info);
-    info->M = h->hist.M;
-    info->converged = 1;
-    info->beta = h->hist.beta;
-    for (int i = 1; i <= h->hist.M; ++i) info->sigma[i - 1] = (int8_t)h->hist.sigma[i];
+  auto* p = new sp2_handle_s::Pending();
+  p->adjoint = true;
+  int code = run_adjoint(h, Gd, 1, 0, 1, dtype, oy.dev, dtype, c, &p->adj_state);
+  if (code == SP2_OK) code = finish_out(h, oy);
+  if (code != SP2_OK) {
+    delete p;
+    return code;
   }
-  fill_timing(c, h->hist.M, info);
-  return SP2_OK;
+  p->c = c;
+  return finish_call(h, p, info, oy.host);
 }
 
 int sp2_release_history(sp2_handle_t h) {
@@ -1425,6 +1618,7 @@ extern "C" {
 int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, double kT,
               const void* B, int64_t K, int b_diag_only, int canonical, int n_doublings,
               const sp2_opts* opts_in, void* D, void* D1, sp2_info* info) {
+  if (h) drop_pending(h);   // this call completes before it returns
   if (!h) return SP2_EINVAL;
   if (N < 0 || K < 0) return fail(h, SP2_EINVAL, "negative size");
   if (dtype != SP2_F64 && dtype != SP2_F32) return fail(h, SP2_EINVAL, "unknown dtype %d", dtype);
@@ -1536,6 +1730,7 @@ extern "C" {
 int sp2_nonorth_susceptibility(sp2_handle_t h, const void* H, const void* S, int64_t N, int dtype,
                                double nocc, const void* A, const sp2_opts* opts_in, void* D,
                                void* WH, void* WS, void* Zout, sp2_info* info) {
+  if (h) drop_pending(h);   // this call completes before it returns
   TRY(check_common(h, H, N, dtype, nocc));
   if (N > 0 && (!S || !A || !D || !WH || !WS)) return fail(h, SP2_EINVAL, "null pointer");
   sp2_opts o = resolve(opts_in);
@@ -1876,6 +2071,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
                      const double* Ksite, const double* Vext, int64_t F, const sp2_scf_opts* so,
                      const sp2_opts* opts_in, double* q_out, double* residuals, int* iterations,
                      double* traj_r, double* traj_q, sp2_info* info) {
+  if (h) drop_pending(h);   // this call completes before it returns
   TRY(check_common(h, H, N, dtype, nocc));
   if (!so) return fail(h, SP2_EINVAL, "null sp2_scf_opts");
   if (norb < 1 || N % norb != 0) return fail(h, SP2_EINVAL, "N must be a multiple of norb");
@@ -1977,6 +2173,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
     Sp2Out rr;
     TRY(run_sp2(h, Hd, N, dtype, nocc, o, pub, F, 1, false, X, Y, c, &rr));
     if (!rr.converged) return fail(h, SP2_ENOCONV, "SP2 did not converge inside the SCF loop");
+    TRY(poll_state(h));   // the branch signs of this run (read below)
     if (o.fixed_m == 0) {
       // H is the same in every iteration: later iterations apply this run's polynomial
       // -- its branches, M and spectral bounds -- so the response map changes only by

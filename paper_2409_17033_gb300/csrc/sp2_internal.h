@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/sp2.h"
@@ -26,6 +27,7 @@ struct DevState {
   double t2[SP2_MAX_ITER + 2];   // ||X_n||_F^2
   double f[SP2_MAX_ITER + 2];    // ||X_n - X_n^2||_F^2, known after step n
   int sigma[SP2_MAX_ITER + 2];   // sigma_n, the branch taken by step n (X_n -> X_{n+1})
+  int plane1[SP2_MAX_ITER + 2];  // split-tail mode: 1 if step n uses the hi planes alone
   int stop_at;                   // M once a stop rule fired, else 0
   int nonfinite;                 // a trace was NaN/Inf
   int abort_flag;                // a device wait timed out (kernel bailed out)
@@ -36,7 +38,10 @@ struct DevState {
   int keep_step;                 // step whose input X_n (and Y_n) is to be kept now
   int backtracked;               // the floor stop returned X_nbest, not the last iterate
   int stop_step;                 // the step after which the stop test fired
+  double alpha, beta;            // X_1 = alpha I + beta H, from the (widened) bounds
 };
+// The host reads the trailing part of DevState (from stop_at on) after every step.
+inline size_t devstate_tail_offset() { return offsetof(DevState, stop_at); }
 
 // Storage of one padded matrix (or a batch of them) in a given mode.
 struct MatBuf {
@@ -124,9 +129,16 @@ struct Tile {       // one output tile of a product kernel
 
 // ---------------------------------------------------------------- launchers
 // elementwise / reduction kernels (kernels_elem.cu)
+// Gershgorin bounds of H into st->bounds (widened for a point spectrum) and the
+// coefficients st->alpha, st->beta of X_1 = alpha I + beta H; NaN/Inf bounds set
+// st->nonfinite and stop the recursion before its first step (stop_at = -1).
 cudaError_t launch_bounds(const void* H, int64_t n, int dtype, double2* part, int nparts,
                           DevState* st, cudaStream_t s);
 int bounds_nparts(int64_t n);
+// the same from given bounds
+cudaError_t launch_set_bounds(DevState* st, double eps_min, double eps_max, cudaStream_t s);
+// preset branch signs sigma_1..sigma_m (m <= SP2_MAX_ITER), passed by value
+cudaError_t launch_set_sigma(DevState* st, const int8_t* sigma, int m, cudaStream_t s);
 
 // X_1 = alpha I + beta H (or Y_1 = beta B for a batch), caller layout -> padded mode layout.
 // diag_only: B given as diagonals (batch x n). symmetrize: use (B + B^T)/2.
@@ -134,9 +146,13 @@ int bounds_nparts(int64_t n);
 // FP16X2: planes are written with scale 1 when ymax is null (X), otherwise only
 // the master is written and max|entry| per batch entry is accumulated into
 // ymax (planes follow from launch_split_scaled).
+// coef: INIT_ARGS uses (alpha, beta); INIT_STATE takes alpha, beta from st;
+// INIT_STATE_BETA takes (0, st->beta).
+enum InitCoef : int { INIT_ARGS = 0, INIT_STATE = 1, INIT_STATE_BETA = 2 };
 cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, int dtype,
                         int diag_only, int symmetrize, double alpha, double beta, int mode,
-                        MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s);
+                        MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s,
+                        int coef = INIT_ARGS, const DevState* st = nullptr);
 int init_nparts(int64_t np);
 
 // reduce trace partials of X_n, decide stop/sigma (see DevState)
@@ -146,6 +162,7 @@ struct DecideParams {
   double nocc, idem_tol, floor_gate;
   int min_iter, max_iter;
   int fixed_m;       // > 0: sigma preset, stop when n - 1 == fixed_m
+  double tail_f;     // > 0: single-plane products while f of the last iterate exceeds it
 };
 cudaError_t launch_decide(const Part3* part, DevState* st, DecideParams p, cudaStream_t s);
 // copy `count` entries of the master src -> dst when st->keep_step == step (the
@@ -161,8 +178,12 @@ cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t
                                int slot_out, cudaStream_t s);
 
 // padded mode layout -> caller layout (N x N per batch entry), times `scale`
+// (times st->beta as well when beta_state is given)
 cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
-                            double scale, void* dst, int dtype, cudaStream_t s);
+                            double scale, void* dst, int dtype, cudaStream_t s,
+                            const DevState* beta_state = nullptr);
+// reset of the fields an adjoint recursion does not use (stop, keep, abort, nonfinite)
+cudaError_t launch_adjoint_state(DevState* st, cudaStream_t s);
 
 // regenerate hi/lo planes from the FP32 master, rows x np (plane scale 1)
 cudaError_t launch_split(MatBuf m, int64_t rows, int64_t np, int mode, cudaStream_t s);
@@ -196,6 +217,8 @@ struct TcTuning {
   int withhold = 0;    // test hook: the first TMA load of CTA 0 is never issued
   int fused_response = 0;  // response step as one EPI_SYMM launch (else EPI_PLAIN + transpose-add)
 };
+// (TcLaunch.tail: the split-tail mode; the kernel reads st->plane1[step] and uses
+// the hi planes alone, one product per segment pair, where it is set.)
 // One product launch: C = P Q (EPI_SQUARE: P = Q = X; EPI_PLAIN: P = stacked A,
 // Q = symmetric B; EPI_SYMM: P = stacked symmetric Y, Q = X, C = Y X + X Y).
 struct TcLaunch {
@@ -214,6 +237,7 @@ struct TcLaunch {
   const float* q_scale = nullptr;  // FP16X2: the plane scale of Q (nullable)
   const float* o_scale = nullptr;  // FP16X2 EPI_SYMM: per batch entry, scale of the output planes
   float* zmax = nullptr;           // FP16X2 EPI_PLAIN: per batch entry, receives max |C|
+  int tail = 0;                    // split-tail mode (st->plane1 decides per step)
   TcTuning tune;
 };
 cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size_t errlen);
