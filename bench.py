@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-resident", action="store_true")
+    ap.add_argument("--no-exact", action="store_true",
+                    help="skip the accuracy report against the FP64 closed forms (host LAPACK)")
     ap.add_argument("--workload", default="chi", choices=["chi", "fermi", "scf", "nonorth"])
     ap.add_argument("--scf-tol", type=float, default=1e-6)
     return ap.parse_args()
@@ -207,13 +209,40 @@ def logical_flops(n: int, m: int, k: int) -> float:
 
 
 def cpu_oracle_sample(n: int, H32: np.ndarray, nocc: float):
-    """One SP2 step of the FP64 oracle at full size (one N^3 product), timed."""
+    """One SP2 step of the FP64 oracle on an n x n Hamiltonian (one n^3 product), timed."""
     from oracle import sp2 as osp2
     H = H32.astype(np.float64)
     t0 = time.perf_counter()
     osp2.sp2_density(H, nocc, sigma=[1])
     dt = time.perf_counter() - t0
     return dt, 2.0 * float(n) ** 3 / dt / 1e12
+
+
+def rel_fro(a, b) -> float:
+    a = np.asarray(a, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cpu_oracle_accuracy(tb, a_diag: np.ndarray, D_gpu: np.ndarray, chi_gpu: np.ndarray,
+                        a1_gpu: np.ndarray, v: np.ndarray) -> dict:
+    """The oracle leg's accuracy report: the FP64 closed forms on the host
+    (LAPACK eigendecomposition; D = theta(mu I - H), chi^A by Daleckii-Krein,
+    a1_k = Tr[chi^A H1_k]) against the solve's outputs, as relative Frobenius
+    errors, with the conditioning kappa = spectral width / HOMO-LUMO gap."""
+    from oracle import exact
+    t0 = time.perf_counter()
+    e, V = exact.eigh(tb.H.astype(np.float64))
+    kappa = float((e[-1] - e[0]) / (e[tb.nocc] - e[tb.nocc - 1]))
+    eD = rel_fro(D_gpu, exact.density_zero_T(e, V, tb.nocc))
+    chi_ex = exact.response_zero_T(e, V, tb.nocc, np.diag(a_diag.astype(np.float64)))
+    del V
+    eC = rel_fro(chi_gpu, chi_ex)
+    a1_ex = np.diagonal(chi_ex) @ v.T.astype(np.float64)
+    del chi_ex
+    return {"D": eD, "chi": eC, "a1": rel_fro(a1_gpu, a1_ex), "kappa": kappa,
+            "gap": float(e[tb.nocc] - e[tb.nocc - 1]),
+            "a1_perturbations": int(v.shape[0]), "host_s": time.perf_counter() - t0,
+            "reference": "FP64 closed forms on the host (LAPACK dsyevd, Daleckii-Krein)"}
 
 
 def chi_config(args, ws: int) -> dict:
@@ -230,27 +259,34 @@ def chi_config(args, ws: int) -> dict:
 
 
 def run_reference(args, ws, rank):
-    """The oracle as it stands on the host cores, on this workload: each step
-    is one FP64 SP2 step (one N x N x N product) at N = args.n."""
+    """The oracle as it stands on the host cores, on this workload. Each step is
+    a bounded sample of the solve: one FP64 oracle SP2 step (one m^3 product,
+    m = N/2) on the leading m x m block of the same Hamiltonian, reported as the
+    solve's metric (TFLOP/s) at that rate."""
     if rank != 0:
         return
     tb, A = workload(args.n, seed=0)
+    m = args.n // 2
+    Hs = np.ascontiguousarray(tb.H[:m, :m])
     for _ in range(args.warmup):
-        cpu_oracle_sample(args.n, tb.H, tb.nocc)
+        cpu_oracle_sample(m, Hs, m // 2)
     times = []
     for _ in range(args.steps):
-        dt, _ = cpu_oracle_sample(args.n, tb.H, tb.nocc)
+        dt, _ = cpu_oracle_sample(m, Hs, m // 2)
         times.append(dt)
     t = sum(times) / len(times)
-    val = 2.0 * float(args.n) ** 3 / t / 1e12
+    val = 2.0 * float(m) ** 3 / t / 1e12
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": chi_config(args, ws),
+        "sample": (f"each step: one FP64 oracle SP2 step (one {m}^3 product) on the leading "
+                   f"{m} x {m} block of the N={args.n} Hamiltonian; the solve's flops at that rate"),
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"one FP64 SP2 step at N={args.n} per step (numpy/BLAS, all host threads)"},
+                         "sample": (f"one FP64 SP2 step ({m}^3 product, {t:.1f} s) per step on the "
+                                    f"leading {m} x {m} block; numpy/BLAS, all host threads")},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -411,11 +447,38 @@ def run_ours(args, ws, rank):
             chi_h, D_h, _ = sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
         e2e_s = (time.perf_counter() - t0) / args.steps
         e2e_s = allmax(ws, e2e_s)
+        # raw pinned copy rates on this machine, for reading the end-to-end overhead
+        scratch = torch.empty_like(H)
+        torch.cuda.synchronize()
+        c0, c1 = _events()
+        c0.record(stream)
+        scratch.copy_(torch.from_numpy(Hh), non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms = c0.elapsed_time(c1)
+        c0.record(stream)
+        torch.from_numpy(kwh["D_out"]).copy_(scratch, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        d2h_ms = c0.elapsed_time(c1)
+        del scratch
         line["e2e"] = {"value": whole_job_tflops(ws, lflops, e2e_s * 1e3), "unit": "TFLOP/s",
                        "h2d_bytes_per_step": int(Hh.nbytes + Ah.nbytes),
                        "d2h_bytes_per_step": int(chi_h.nbytes + D_h.nbytes),
-                       "ms_per_step": e2e_s * 1e3}
+                       "ms_per_step": e2e_s * 1e3,
+                       "pinned_copy_gbs": {"h2d": Hh.nbytes / (h2d_ms * 1e-3) / 1e9,
+                                           "d2h": D_h.nbytes / (d2h_ms * 1e-3) / 1e9}}
         del hh
+
+    if rank == 0 and ws == 1 and not args.no_exact:
+        # accuracy of this solve against the FP64 closed forms (the oracle leg, host LAPACK);
+        # a1 over 64 site-potential perturbations, contracted on the device
+        import workloads
+        v = workloads.tb_site_potentials(tb, 64, seed=1)
+        a1 = sp2.response_contract(chi, torch.from_numpy(v.astype(np.float32)).cuda(),
+                                   diag_only=True, handle=h)[0].cpu().numpy()
+        acc = cpu_oracle_accuracy(tb, A[0], D.cpu().numpy(), chi[0].cpu().numpy(), a1, v)
+        line["quality"]["rel_err_vs_exact"] = acc
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         dt, tf = cpu_oracle_sample(n, tb.H, tb.nocc)
