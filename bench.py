@@ -20,6 +20,9 @@ Two further workloads print their own JSON line (one GPU, not run by default):
   --workload nonorth  N=8192 non-orthonormal basis (Sec. V.A): the dual weights
                     W_H, W_S once, then three contractions per basis-set
                     dependent perturbation, against one primal response each.
+  --workload configs  the other configurations: N=128 microseconds per SP2
+                    iteration, N=4096 primal (64 H1) vs dual (4 A) in FP16X2 /
+                    FP32 / FP64, N=16384 through torch.autograd vs direct.
   --workload scf    N=4096 tight-binding, 128 site fields: self-consistent
                     response (Eq. DM_CP_SCF) with linear, Anderson and the
                     learned MLP mixer (trained here on 96 fields' linear-mixing
@@ -61,7 +64,8 @@ def parse():
     ap.add_argument("--no-resident", action="store_true")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the accuracy report against the FP64 closed forms (host LAPACK)")
-    ap.add_argument("--workload", default="chi", choices=["chi", "fermi", "scf", "nonorth"])
+    ap.add_argument("--workload", default="chi",
+                    choices=["chi", "fermi", "scf", "nonorth", "configs"])
     ap.add_argument("--scf-tol", type=float, default=1e-6)
     return ap.parse_args()
 
@@ -580,11 +584,13 @@ def run_fermi(args, ws, rank):
 def run_scf(args, ws, rank):
     """Self-consistent response on the N=4096 tight-binding workload (1024
     sites x 4 orbitals) for 128 site fields V_ext ~ N(0, 0.1^2): fields 0..95
-    train the learned mixer, fields 96..127 are held out. Responses in FP16X2,
-    whose rounding floors the residual near 3e-6 at this size: the mixers are
-    compared to 1e-5; Anderson and the MLP mixer then also run to the target
-    (1e-6) with the iterations below 1e-5 in FP32 responses. The residual is
-    the plain method's in every case. Kernels: the regularised
+    train the learned mixer, fields 96..127 are held out. Mixers: linear
+    (alpha 0.3 and 0.7), Anderson, the learned correction on a unit step, and
+    Anderson with that learned step as its preconditioner. Responses in FP16X2,
+    whose rounding floors the residual near 3e-6 at this size; below 1e-5 every
+    mixer continues in BF16X3 responses (24-bit operands, FP32 accumulation) with
+    the same SP2 polynomial, to the target residual (1e-6). The residual is the
+    plain method's in every case. Kernels: the regularised
     K_ab = 1/sqrt(r_ab^2 + 1) (positive definite) for the mixer comparison,
     and the literal K_ab = 1/r_ab, whose fixed-point map is unstable (linear
     mixing diverges; reported as measured)."""
@@ -644,28 +650,23 @@ def run_scf(args, ws, rank):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     res = {}
-    mixers = (("linear", dict(mixer="linear", alpha=alpha), 60),
-              ("linear_alpha0.7", dict(mixer="linear", alpha=0.7), 60),
-              ("anderson", dict(mixer="anderson", alpha=alpha, history=8), 40),
-              ("mlp", dict(mixer="mlp", alpha=a_mlp, W1=W1, W2=W2, bf16_infer=True), 60))
+    refine = "bf16x3"
+    mixers = (("linear", dict(mixer="linear", alpha=alpha), 150),
+              ("linear_alpha0.7", dict(mixer="linear", alpha=0.7), 80),
+              ("anderson", dict(mixer="anderson", alpha=alpha, history=8), 60),
+              ("mlp", dict(mixer="mlp", alpha=a_mlp, W1=W1, W2=W2, bf16_infer=True), 80),
+              ("anderson_mlp", dict(mixer="anderson_mlp", alpha=a_mlp, history=8, W1=W1, W2=W2,
+                                    bf16_infer=True), 60))
     for name, kw, cap in mixers:
-        (q, r, it, _, inf), t = timed(K=Kreg, Vext=test, tol=floor_tol, max_iter=cap, **kw)
-        res[name] = {"iterations": it, "final_residual": float(r[-1]), "ms": t,
-                     "converged": bool(r[-1] <= floor_tol), "q": q}
+        (q, r, it, _, inf), t = timed(K=Kreg, Vext=test, tol=tol, max_iter=cap, refine_mode=refine,
+                                      refine_below=floor_tol, **kw)
+        res[name] = {"iterations": it, "split_iterations": inf["refine_iter"],
+                     "final_residual": float(r[-1]), "ms": t, "converged": bool(r[-1] <= tol),
+                     "residuals": [float(x) for x in r], "q": q}
     qa = res["anderson"]["q"]
     for name in res:
         q = res[name].pop("q")
         res[name]["q_rel_diff_vs_anderson"] = float((q - qa).norm() / qa.norm())
-    # below the FP16X2 floor: the remaining iterations in FP32 responses (FP32 converges
-    # its own SP2 polynomial, so the residual first jumps to the FP16X2/FP32 map difference)
-    refined = {}
-    for name, kw in (("anderson", dict(mixer="anderson", alpha=alpha, history=8)),
-                     ("mlp", dict(mixer="mlp", alpha=a_mlp, W1=W1, W2=W2, bf16_infer=True))):
-        (q, r, it, _, inf), t = timed(K=Kreg, Vext=test, tol=tol, max_iter=30, refine_mode="fp32",
-                                      refine_below=floor_tol, **kw)
-        refined[name] = {"iterations": it, "fp16x2_iterations": inf["refine_iter"],
-                         "final_residual": float(r[-1]), "converged": bool(r[-1] <= tol), "ms": t,
-                         "residuals": [float(x) for x in r]}
     lit = {}
     for name, kw, cap in (("linear", dict(mixer="linear", alpha=alpha), 12),
                           ("anderson", dict(mixer="anderson", alpha=alpha, history=8), 30)):
@@ -673,18 +674,18 @@ def run_scf(args, ws, rank):
         lit[name] = {"iterations": it, "final_residual": float(r[-1]), "ms": t,
                      "converged": bool(r[-1] <= floor_tol), "residuals": [float(x) for x in r]}
     line = {
-        "metric": "N=4096 SCF response, 128 fields: iterations to residual 1e-5 (MLP vs linear vs Anderson)",
+        "metric": f"N=4096 SCF response, 128 fields: iterations to residual {tol:g} (MLP vs linear vs Anderson)",
         "value": res["linear"]["iterations"] / max(res["mlp"]["iterations"], 1),
         "unit": "x (linear alpha=0.3 iterations / MLP iterations, 32 held-out fields)",
         "n_gpus": 1, "higher_is_better": True,
-        "dtype": "fp16x2 responses (fp32 in the refined runs); MLP fp32 train, bf16 infer",
+        "dtype": f"fp16x2 responses, {refine} below {floor_tol:g}; MLP fp32 train, bf16 infer",
         "data": "synthetic",
         "config": {"workload": "tight-binding N=4096 (1024 sites x 4), 128 fields V_ext~N(0,0.1^2): "
                                "96 train / 32 held out; MLP 1024->256->1024 ReLU, no biases, "
                                "on a unit linear step",
                    "n": n, "tol": tol, "alpha": alpha, "alpha_mlp": a_mlp,
-                   "refine_below": floor_tol},
-        "regularised_K": res, "regularised_K_refined_to_tol": refined, "literal_K": lit,
+                   "refine_below": floor_tol, "refine_mode": refine},
+        "regularised_K": res, "literal_K": lit,
         "training": {"solution_anderson_iterations": it_star, "solution_residual": float(r_star[-1]),
                      "solution_ms": t_star, "trajectory_iterations": it_tr, "trajectory_ms": t_tr,
                      "pairs": int(X.shape[0]), "adam_steps": 2000, "train_s": t_train,
@@ -773,6 +774,124 @@ def run_nonorth(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_configs(args, ws, rank):
+    """The other configurations of the metric as measurement lines (one GPU):
+    config 1, N=128 gapped random spectrum (FP64 to idem_tol 1e-10, and FP16X2):
+    ms per solve and microseconds per SP2 iteration of the density, the backward
+    susceptibility and the 8 responses; config 2, N=4096 tight binding: the primal
+    form (64 site-potential responses, then Tr[A_l D1_k]) against the dual form
+    (chi of the 4 observables, then Tr[chi_l H1_k]) in FP16X2, FP32 and FP64 (FP64
+    extrapolated from per-product event times); config 3, N=16384: the forward
+    SP2 + adjoint through torch.autograd (SP2Density, dense incoming gradient)
+    beside the direct backward susceptibility call."""
+    import torch
+
+    import paper_2409_17033_gb300 as sp2
+    import workloads
+    stream = torch.cuda.current_stream()
+    h = sp2.Handle()
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record(stream)
+        r = None
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    out = {"config1": {}, "config2": {}, "config3": {}}
+    # ---------------------------------------------------------------- config 1
+    p = workloads.random_spectrum(128, nocc=64, k=8, seed=0)
+    for mode, dt in (("fp64", torch.float64), ("fp16x2", torch.float32)):
+        H = torch.from_numpy(p.H).to(dt).cuda()
+        A = torch.from_numpy(p.A[None]).to(dt).cuda()
+        H1 = torch.from_numpy(p.H1).to(dt).cuda()
+        kw = dict(mode=mode, handle=h, idem_tol=1e-10 if mode == "fp64" else 0.0)
+        t_d, (_, inf) = timed(lambda: sp2.sp2_density(H, p.nocc, **kw), reps=20)
+        t_c, _ = timed(lambda: sp2.sp2_susceptibility(H, p.nocc, A, "backward", **kw), reps=20)
+        t_r, _ = timed(lambda: sp2.sp2_response(H, p.nocc, H1, **kw), reps=20)
+        m = inf["M"]
+        out["config1"][mode] = {"M": m, "density_ms": t_d, "density_us_per_iteration": 1e3 * t_d / m,
+                                "backward_chi_ms": t_c, "responses8_ms": t_r,
+                                "responses8_us_per_iteration": 1e3 * t_r / m}
+    # ---------------------------------------------------------------- config 2
+    tb = workloads.tight_binding(4096, seed=0, dtype=np.float32)
+    A4 = workloads.tb_dipole_observables(tb)                  # (4, N) diagonals
+    v = workloads.tb_site_potentials(tb, 64, seed=1)         # (64, N) diagonals
+    for mode, dt in (("fp16x2", torch.float32), ("fp32", torch.float32), ("fp64", torch.float64)):
+        H = torch.from_numpy(tb.H).to(dt).cuda()
+        Ad = torch.from_numpy(A4).to(dt).cuda()
+        vd = torch.from_numpy(v).to(dt).cuda()
+        if mode != "fp64":
+            def primal():
+                D1, _, inf = sp2.sp2_response(H, tb.nocc, vd, diag_only=True, mode=mode, handle=h)
+                return sp2.response_contract(D1, Ad, diag_only=True, handle=h), inf
+            def dual():
+                chi, _, inf = sp2.sp2_susceptibility(H, tb.nocc, Ad, "backward", diag_only=True,
+                                                     mode=mode, handle=h)
+                return sp2.response_contract(chi, vd, diag_only=True, handle=h), inf
+            t_p, (a_p, inf_p) = timed(primal)
+            t_q, (a_q, inf_q) = timed(dual)
+            a_p = a_p.cpu().numpy().T      # (4, 64)
+            a_q = a_q.cpu().numpy()
+            out["config2"][mode] = {"M": inf_q["M"], "primal_ms": t_p, "dual_ms": t_q,
+                                    "primal_over_dual": t_p / t_q,
+                                    "a1_primal_vs_dual": float(np.linalg.norm(a_p - a_q) / np.linalg.norm(a_q))}
+        else:
+            # one square and one 64-response step (fixed branch), event-timed, times the
+            # product counts of this mode's converged run (M from a density solve)
+            _, inf_d = sp2.sp2_density(H, tb.nocc, mode="fp64", idem_tol=1e-10, handle=h)
+            m = inf_d["M"]
+            _, inf_s = sp2.sp2_density(H, tb.nocc, mode="fp64", sigma=[1], time_kernels=True, handle=h)
+            _, _, inf_y = sp2.sp2_response(H, tb.nocc, vd, diag_only=True, mode="fp64", sigma=[1],
+                                           time_kernels=True, handle=h)
+            _, _, inf_a = sp2.sp2_susceptibility(H, tb.nocc, Ad, "forward", diag_only=True,
+                                                 mode="fp64", sigma=[1], time_kernels=True, handle=h)
+            sq = inf_s["product_ms"]
+            y64 = inf_y["product_ms"] - sq
+            y4 = inf_a["product_ms"] - sq
+            rec = m - (m + 3) // 4
+            out["config2"][mode] = {"M": m, "primal_ms_extrapolated": m * (sq + y64),
+                                    "dual_ms_extrapolated": (m + rec) * sq + m * y4,
+                                    "primal_over_dual": m * (sq + y64) / ((m + rec) * sq + m * y4),
+                                    "note": "per-product event times x product counts"}
+        del H
+    # ---------------------------------------------------------------- config 3
+    n = 16384
+    tb3, A3 = workload(n, seed=0)
+    H = torch.from_numpy(tb3.H).cuda()
+    a = torch.from_numpy(A3[0]).cuda()
+    Ad = torch.from_numpy(A3).cuda()
+    hh = sp2.Handle()
+
+    def via_autograd():
+        Hg = H.clone().requires_grad_(True)
+        D = sp2.sp2_density_autograd(Hg, tb3.nocc, mode="fp16x2", ckpt_k=4, handle=hh)
+        loss = (D.diagonal() * a).sum()          # Tr[A D], A the x-dipole
+        loss.backward()
+        return Hg.grad
+
+    def direct():
+        chi, _, _ = sp2.sp2_susceptibility(H, tb3.nocc, Ad, "backward", diag_only=True,
+                                           mode="fp16x2", ckpt_k=4, handle=hh)
+        return chi[0]
+
+    t_a, g = timed(via_autograd)
+    t_b, chi = timed(direct)
+    out["config3"] = {"autograd_ms": t_a, "direct_ms": t_b,
+                      "grad_vs_direct_chi_max_abs": float((g - chi).abs().max()),
+                      "chi_max_abs": float(chi.abs().max()),
+                      "note": "autograd: forward SP2 (keep_history, k=4), dense incoming gradient "
+                              "diag(A) of Tr[A D], adjoint (Eq. DM2); direct: the diagonal A"}
+    line = {"metric": "configs 1-3: N=128 us per SP2 iteration; N=4096 primal vs dual; "
+                      "N=16384 autograd vs direct", "n_gpus": 1, "data": "synthetic", **out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = (1, 0, 0)
@@ -788,6 +907,8 @@ def main():
         run_nonorth(args, ws, rank)
     elif args.workload == "scf":
         run_scf(args, ws, rank)
+    elif args.workload == "configs":
+        run_configs(args, ws, rank)
     else:
         run_ours(args, ws, rank)
     if ws > 1:

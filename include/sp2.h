@@ -325,14 +325,21 @@ int sp2_nonorth_susceptibility(sp2_handle_t h, const void* H, const void* S, int
  * mentions), or a learned correction to linear mixing,
  * q <- q + alpha r + ||r|| MLP(r / ||r||), r = q_out - q, with
  * y = W2 relu(W1 x) (no biases; W1: hidden x n_sites, W2: n_sites x hidden,
- * device FP32; bf16_infer rounds weights and activations to bfloat16).
+ * device FP32; bf16_infer rounds weights and activations to bfloat16), or
+ * Anderson with that learned step as its preconditioner (SP2_MIX_ANDERSON_MLP).
  * The residual judging convergence is the plain method's:
  * ||q_out(q) - q||_2 / ||q_out(0)||_2 over all fields, stopping at <= tol.
  * K, V_ext and q (F x n_sites out, the last iterate) are double, device or
  * host. residuals: host array of max_iter doubles (nullable); iterations:
  * host int. traj_r / traj_q (nullable, device doubles of max_iter x F x
  * n_sites): residual and iterate of every iteration (training data). */
-typedef enum { SP2_MIX_LINEAR = 0, SP2_MIX_ANDERSON = 1, SP2_MIX_MLP = 2 } sp2_mixer;
+typedef enum {
+  SP2_MIX_LINEAR = 0,
+  SP2_MIX_ANDERSON = 1,
+  SP2_MIX_MLP = 2,
+  SP2_MIX_ANDERSON_MLP = 3  /* Anderson with the learned step as its preconditioner:
+                               q <- sum_i c_i (q_i + P(r_i)), P(r) = alpha r + ||r|| MLP(r/||r||) */
+} sp2_mixer;
 
 typedef struct {
   int mixer;            /* sp2_mixer */
@@ -347,10 +354,12 @@ typedef struct {
   int refine_mode;      /* sp2_mode of the responses after the switch below */
   double refine_below;  /* > 0: once the residual is <= refine_below, or has not reached a
                            new minimum for 3 iterations, the remaining iterations compute
-                           the responses in refine_mode: its own SP2 run fixes the branches
-                           and M again, and Anderson restarts its history. 0 = never
-                           switch. Lets split-precision responses do the bulk of the
-                           iterations and FP32 / FP64 ones go below their rounding floor. */
+                           the responses in refine_mode, and Anderson restarts its history.
+                           The SP2 polynomial (branches, M, bounds) of the first iterations
+                           is kept, except for SP2_MODE_FP64, whose own SP2 run fixes it again
+                           (to its tighter floor). 0 = never switch. Lets split-precision
+                           responses do the bulk of the iterations and FP32 / FP64 ones go
+                           below their rounding floor. */
   double kT;            /* > 0: finite-temperature responses (Sec. V.B recursion, as in
                            sp2_fermi) at chemical potential mu; 0: zero temperature (Eq. DM1) */
   double mu;

@@ -23,6 +23,9 @@ q <- q + alpha r + ||r|| MLP(r / ||r||) (the map is positively homogeneous,
 so this equals q + alpha r + MLP(r)); trained on (r_i / ||r_i||,
 (q* - q_i - alpha r_i) / ||r_i||) pairs it learns the slow modes that linear
 mixing leaves, and an untrained (zero) MLP is plain linear mixing.
+anderson_mlp: Anderson with that learned step as its preconditioner,
+q <- sum_i c_i (q_i + P(r_i)), P(r) = alpha r + ||r|| MLP(r / ||r||), the c_i as
+for Anderson; a zero network gives Anderson, a history of one the MLP mixer.
 """
 from __future__ import annotations
 
@@ -78,7 +81,7 @@ def scf_iterate(chi0, K, Vext, mixer="linear", alpha=0.3, hist=8, tol=1e-6, max_
     q = np.zeros_like(Vext)
     res = []
     norm0 = None
-    qs, rs = [], []
+    qs, rs, ps = [], [], []     # iterates, residuals and preconditioned steps of the history
     for it in range(max_iter):
         qout = (chi0 @ (Vext + q @ K.T).T).T
         r = qout - q
@@ -89,10 +92,17 @@ def scf_iterate(chi0, K, Vext, mixer="linear", alpha=0.3, hist=8, tol=1e-6, max_
             break
         if mixer == "linear":
             q = q + alpha * r
-        elif mixer == "anderson":
+        elif mixer in ("anderson", "anderson_mlp"):
             qs.append(q.copy())
             rs.append(r.copy())
-            qs, rs = qs[-hist:], rs[-hist:]
+            if mixer == "anderson":
+                ps.append(alpha * r)
+            else:
+                W1, W2 = mlp
+                nr = np.linalg.norm(r, axis=1, keepdims=True)
+                x = r / np.where(nr > 0, nr, 1.0)
+                ps.append(alpha * r + nr * mlp_forward(W1, W2, x))
+            qs, rs, ps = qs[-hist:], rs[-hist:], ps[-hist:]
             new = np.zeros_like(q)
             for f in range(q.shape[0]):
                 R = np.stack([x[f] for x in rs])          # m x ns
@@ -106,7 +116,7 @@ def scf_iterate(chi0, K, Vext, mixer="linear", alpha=0.3, hist=8, tol=1e-6, max_
                 rhs = np.zeros(m + 1)
                 rhs[m] = 1.0
                 c = np.linalg.solve(A, rhs)[:m]
-                new[f] = sum(c[i] * (qs[i][f] + alpha * rs[i][f]) for i in range(m))
+                new[f] = sum(c[i] * (qs[i][f] + ps[i][f]) for i in range(m))
             q = new
         elif mixer == "mlp":
             W1, W2 = mlp

@@ -119,7 +119,7 @@ class ScfOpts(C.Structure):
     ]
 
 
-MIXERS = {"linear": 0, "anderson": 1, "mlp": 2}
+MIXERS = {"linear": 0, "anderson": 1, "mlp": 2, "anderson_mlp": 3}
 
 EXPORTS = {
     "sp2_default_opts": (None, [C.POINTER(Opts)]),

@@ -2077,11 +2077,13 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   if (norb < 1 || N % norb != 0) return fail(h, SP2_EINVAL, "N must be a multiple of norb");
   if (F < 1 || !Ksite || !Vext || !q_out) return fail(h, SP2_EINVAL, "bad SCF arguments");
   if (so->max_iter < 1) return fail(h, SP2_EINVAL, "max_iter < 1");
-  if (so->mixer == SP2_MIX_ANDERSON && (so->history < 1 || so->history > 32))
+  const bool anderson = so->mixer == SP2_MIX_ANDERSON || so->mixer == SP2_MIX_ANDERSON_MLP;
+  const bool learned = so->mixer == SP2_MIX_MLP || so->mixer == SP2_MIX_ANDERSON_MLP;
+  if (anderson && (so->history < 1 || so->history > 32))
     return fail(h, SP2_EINVAL, "Anderson history outside 1..32");
-  if (so->mixer == SP2_MIX_MLP && (!so->W1 || !so->W2 || so->hidden < 1))
+  if (learned && (!so->W1 || !so->W2 || so->hidden < 1))
     return fail(h, SP2_EINVAL, "MLP mixer needs W1, W2 and hidden");
-  if (so->mixer < 0 || so->mixer > 2) return fail(h, SP2_EINVAL, "unknown mixer");
+  if (so->mixer < 0 || so->mixer > 3) return fail(h, SP2_EINVAL, "unknown mixer");
   const bool finite_t = so->kT > 0.0;
   const int ndbl = so->n_doublings > 0 ? so->n_doublings : 20;
   if (finite_t && (!std::isfinite(so->mu) || ndbl > 64))
@@ -2112,8 +2114,13 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   double *q = static_cast<double*>(pq), *qo = static_cast<double*>(pqo), *r = static_cast<double*>(pr);
   double* u = static_cast<double*>(pu);
   double* norms = static_cast<double*>(pn);
-  const int m = so->mixer == SP2_MIX_ANDERSON ? so->history : 0;
-  double *Qh = nullptr, *Rh = nullptr, *G = nullptr, *cf = nullptr;
+  const int m = anderson ? so->history : 0;
+  double *Qh = nullptr, *Rh = nullptr, *G = nullptr, *cf = nullptr, *Ph = nullptr;
+  if (so->mixer == SP2_MIX_ANDERSON_MLP) {
+    void* a;
+    TRY(ws(h, "scf.Ph", (size_t)m * tot * sizeof(double), &a));
+    Ph = static_cast<double*>(a);
+  }
   if (m > 0) {
     void *a, *b, *c2, *d;
     TRY(ws(h, "scf.Qh", (size_t)m * tot * sizeof(double), &a));
@@ -2127,7 +2134,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
   }
   float *mx = nullptr, *my = nullptr, *mh = nullptr;
   double* nr = nullptr;
-  if (so->mixer == SP2_MIX_MLP) {
+  if (learned) {
     void *a, *b, *c2, *d;
     TRY(ws(h, "scf.mx", tot * sizeof(float), &a));
     TRY(ws(h, "scf.my", tot * sizeof(float), &b));
@@ -2217,9 +2224,11 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       // the following iterations compute the responses in refine_mode
       o.mode = so->refine_mode;
       TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
-      if (frozen_here) {
-        // the refined arithmetic converges its own SP2 polynomial once (stop rule),
-        // which is then fixed again
+      if (frozen_here && so->refine_mode == SP2_MODE_FP64) {
+        // FP64 converges its own SP2 polynomial once (stop rule, to its tighter floor),
+        // which is then fixed again. Other arithmetic keeps the polynomial of the split
+        // run: a precision floor reached earlier would shorten it and move the response
+        // map (the residual jumps to the difference of the two maps).
         o.fixed_m = 0;
         o.sigma_in = nullptr;
         o.eps_min = o.eps_max = 0.0;
@@ -2230,16 +2239,26 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       a0 = it + 1;  // the new Anderson history holds only residuals of the refined arithmetic
       since_best = 0;
     }
-    if (so->mixer == SP2_MIX_LINEAR || (so->mixer == SP2_MIX_ANDERSON && it < a0)) {
+    if (so->mixer == SP2_MIX_LINEAR || (anderson && it < a0)) {
       CK(launch_axpy_d(q, so->alpha, r, tot, h->stream));
       c.kernels++;
-    } else if (so->mixer == SP2_MIX_ANDERSON) {
+    } else if (anderson) {
       const int ia = it - a0;
       const int slot = ia % m, me = ia + 1 < m ? ia + 1 : m;
       CK(cudaMemcpyAsync(Qh + (size_t)slot * tot, q, tot * sizeof(double), cudaMemcpyDeviceToDevice,
                          h->stream));
       CK(cudaMemcpyAsync(Rh + (size_t)slot * tot, r, tot * sizeof(double), cudaMemcpyDeviceToDevice,
                          h->stream));
+      if (Ph) {
+        // the learned step as Anderson's preconditioner: P(r) = alpha r + ||r|| MLP(r / ||r||)
+        double* p = Ph + (size_t)slot * tot;
+        CK(launch_normalise_rows(r, F, ns, mx, nr, h->stream));
+        TRY(mlp_fwd(h, so->W1, so->W2, (int)ns, so->hidden, mx, F, mh, my, so->bf16_infer));
+        CK(cudaMemsetAsync(p, 0, tot * sizeof(double), h->stream));
+        CK(launch_axpy_d(p, so->alpha, r, tot, h->stream));
+        CK(launch_apply_update(p, my, nr, F, ns, h->stream));
+        c.kernels += 5;
+      }
       CK(launch_gram(Rh, me, F, ns, tot, G, h->stream));
       Gh.resize((size_t)F * me * me);
       ch.resize((size_t)F * me);
@@ -2249,7 +2268,9 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       for (int64_t f = 0; f < F; ++f) anderson_coeffs(&Gh[(size_t)f * me * me], me, &ch[(size_t)f * me]);
       CK(cudaMemcpyAsync(cf, ch.data(), ch.size() * sizeof(double), cudaMemcpyHostToDevice,
                          h->stream));
-      CK(launch_anderson_combine(Qh, Rh, cf, me, F, ns, tot, so->alpha, q, h->stream));
+      // q = sum_i c_i (q_i + alpha r_i), or sum_i c_i (q_i + P(r_i)) with the learned step
+      CK(launch_anderson_combine(Qh, Ph ? Ph : Rh, cf, me, F, ns, tot, Ph ? 1.0 : so->alpha, q,
+                                 h->stream));
       CK(cudaStreamSynchronize(h->stream));  // ch is reused next iteration
       c.kernels += 2;
     } else {

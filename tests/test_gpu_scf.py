@@ -97,6 +97,29 @@ def test_scf_mlp_mixer_matches_oracle_step_by_step(pkg, small, net):
     assert rel(q, q_or) < 1e-6
 
 
+def test_scf_anderson_with_learned_step_matches_oracle(pkg, small):
+    """Anderson with the learned step as its preconditioner on the GPU (FP64
+    responses, FP32 network) against the oracle's anderson_mlp branch with the
+    same weights, residual by residual; Anderson's coefficients amplify the
+    FP32 network's rounding late in the run, as for plain Anderson."""
+    tb, chi0, K, Vx = small
+    ns = chi0.shape[0]
+    rng = np.random.default_rng(6)
+    W1 = (rng.standard_normal((32, ns)) / np.sqrt(ns)).astype(np.float32)
+    W2 = (0.05 * rng.standard_normal((ns, 32)) / np.sqrt(32)).astype(np.float32)
+    H = torch.from_numpy(tb.H).cuda()
+    q, res, its, _ = pkg.sp2_scf_response(
+        H, tb.nocc, 4, K, Vx, mixer="anderson_mlp", alpha=0.3, history=8, tol=1e-9, max_iter=200,
+        W1=torch.from_numpy(W1).cuda(), W2=torch.from_numpy(W2).cuda(), bf16_infer=False,
+        mode="fp64", idem_tol=1e-13)
+    q_or, res_or = scf.scf_iterate(chi0, K, Vx, mixer="anderson_mlp", alpha=0.3, hist=8, tol=1e-9,
+                                   max_iter=200, mlp=(W1.astype(np.float64), W2.astype(np.float64)))
+    assert abs(its - len(res_or)) <= 1
+    k = min(its, len(res_or))
+    assert np.allclose(res[:k], res_or[:k], rtol=1e-3, atol=1e-10)
+    assert rel(q, scf.scf_exact(chi0, K, Vx)) < 1e-7
+
+
 def test_scf_split_precision(pkg, small):
     tb, chi0, K, Vx = small
     H = torch.from_numpy(tb.H).float().cuda()
