@@ -218,11 +218,18 @@ size_t sp2_workspace_bytes(sp2_handle_t h);
  *                             transpose-add pass); 0 (default): Y X, then the
  *                             transpose-add kernel. Same arithmetic up to rounding
  *                             order.
+ *   SP2_OPTION_PAIR_TILES     != 0 (default): the split modes' products run on
+ *                             pairs of SMs (a thread-block cluster of two), each
+ *                             pair computing 256 x 256 output tiles with one
+ *                             tensor-core instruction stream over both SMs; 0: one
+ *                             SM per 128 x 256 tile. Same arithmetic and summation
+ *                             order, hence the same results.
  * Returns SP2_EINVAL for an unknown option or a value out of range. */
 typedef enum {
   SP2_OPTION_WAIT_LIMIT_NS = 0,
   SP2_OPTION_WITHHOLD_LOAD = 1,
-  SP2_OPTION_FUSED_RESPONSE = 2
+  SP2_OPTION_FUSED_RESPONSE = 2,
+  SP2_OPTION_PAIR_TILES = 3
 } sp2_option;
 int sp2_set_option(sp2_handle_t h, int option, int64_t value);
 

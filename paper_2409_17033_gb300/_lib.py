@@ -28,7 +28,7 @@ MODES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16x2": MODE_BF16X2, "fp16x2": 
          "bf16x3": MODE_BF16X3}
 CKPT_AUTO = -1   # SP2_CKPT_AUTO
 # sp2_option
-OPTION_WAIT_LIMIT_NS, OPTION_WITHHOLD_LOAD, OPTION_FUSED_RESPONSE = 0, 1, 2
+OPTION_WAIT_LIMIT_NS, OPTION_WITHHOLD_LOAD, OPTION_FUSED_RESPONSE, OPTION_PAIR_TILES = 0, 1, 2, 3
 
 
 class Opts(C.Structure):

@@ -118,9 +118,10 @@ class Handle:
 
     def set_option(self, option: str, value: int):
         """Product-kernel launch settings (sp2_set_option): "wait_limit_ns",
-        "withhold_load" (test hook of the timed-out wait path) or "fused_response"."""
+        "withhold_load" (test hook of the timed-out wait path), "fused_response" or
+        "pair_tiles"."""
         code = {"wait_limit_ns": L.OPTION_WAIT_LIMIT_NS, "withhold_load": L.OPTION_WITHHOLD_LOAD,
-                "fused_response": L.OPTION_FUSED_RESPONSE}[option]
+                "fused_response": L.OPTION_FUSED_RESPONSE, "pair_tiles": L.OPTION_PAIR_TILES}[option]
         self.check(self.lib.sp2_set_option(self.h, code, int(value)))
 
     def workspace_bytes(self) -> int:

@@ -3,13 +3,14 @@
 // Computes the products of the SP2 path with the hi/lo splitting of Eq.
 // doubleHalf and the three-product form of Eq. MixPrecMult / Eq. mults (lo*lo
 // dropped):
-//     P Q ~ P_hi Q_hi + P_hi Q_lo + P_lo Q_hi,
-// evaluated over a concatenated K axis, [P_hi | P_hi | P_lo] . [Q_hi ; Q_lo ; Q_hi],
-// into FP32 accumulators in tensor memory. Every right factor Q is symmetric,
-// so its row-major planes are directly the K-major B operand.
+//     P Q ~ P_hi Q_lo + P_lo Q_hi + P_hi Q_hi,
+// evaluated over a concatenated K axis, [P_hi | P_lo | P_hi] . [Q_lo ; Q_hi ; Q_hi],
+// into FP32 accumulators in tensor memory: the smaller terms first, hi*hi last.
+// Every right factor Q is symmetric, so its row-major planes are directly the
+// K-major B operand.
 //   BF16X2: bfloat16 planes, one weight for all segments.
 //   BF16X3: three bfloat16 planes (hi + mid + lo = the FP32 value) and six
-//           segments [P_h|P_h|P_m|P_h|P_m|P_l] . [Q_h;Q_m;Q_h;Q_l;Q_m;Q_h]: every
+//           segments [P_l|P_m|P_h|P_m|P_h|P_h] . [Q_h;Q_m;Q_l;Q_h;Q_m;Q_h]: every
 //           term down to 2^-16 relative, no scaling.
 //   FP16X2: the lo planes hold residuals times 2^11; chunks of the hi*lo and
 //           lo*hi segments are weighted by 2^-11 when they are drained from
@@ -28,15 +29,26 @@
 //               pass. Partials of ||Y_{n+1}||_F^2 per tile (FP16X2 plane scales).
 //
 // CTA tile 128 x 256, K step 64 (one 128-byte swizzle row of 16-bit values),
-// 4-stage TMA -> shared-memory
-// ring guarded by mbarriers. Persistent: one CTA per SM walks tiles b, b+G,
-// b+2G, ... of a static list. The K axis is accumulated in 256-wide chunks,
-// alternately in two TMEM buffers, and each chunk is added into FP32 registers
-// by the epilogue warps (the tensor core's own FP32 accumulation truncates).
+// 4-stage TMA -> shared-memory ring guarded by mbarriers. Persistent: one CTA
+// per SM walks tiles b, b+G, b+2G, ... of a static list. The K axis is
+// accumulated in chunks, alternately in two TMEM buffers, and each chunk is
+// added into FP32 registers by the epilogue warps (the tensor core's own FP32
+// accumulation truncates, with a bias that grows with the chunk): 256-wide for
+// hi*hi, up to 2048-wide for the cross terms, whose weighted size is 2^-8 of it
+// or less. A tile starts with the long chunks, so the spare TMEM buffer covers
+// the previous tile's stores.
+//
+// CTA pairs (CG = 2, a cluster of two): a 256 x 256 tile per pair, one
+// tcgen05.mma.cta_group::2 stream of M = 256 issued by rank 0. Each CTA loads
+// its own 128 rows of the A tile and 128 rows of the B tile into a 6-stage ring
+// of 32 KB stages and drains its own 128 accumulator rows; rank 1's warp 1
+// passes each landed stage on to rank 0's barrier, and rank 1's epilogue warps
+// report drained TMEM buffers there. Same arithmetic and order as one SM.
 //
 // Warp roles:
 //   warp 0  (one thread)  TMA producer
-//   warp 1  (one thread)  tcgen05.mma issuer; the whole warp owns the TMEM allocation
+//   warp 1  (one thread)  tcgen05.mma issuer (pair: rank 1's relays stages); the
+//                         whole warp owns the TMEM allocation
 //   warps 2-17            epilogue: tcgen05.ld of each chunk (warp w reads TMEM lanes
 //                         32*(w%4) .. +31, the 64 columns of group (w-2)/4), then
 //                         the epilogue above. With 64 columns per thread the chunk
@@ -58,13 +70,20 @@ namespace sp2 {
 
 namespace {
 
-constexpr int BM = 128;
+constexpr int BM = 128;        // output rows per CTA (a CTA pair's tile has 2 BM)
 constexpr int BN = 256;
 constexpr int BK = 64;
-constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+// Per-CTA ring geometry for CG CTAs per tile: a CTA of a pair holds half of the
+// right factor's rows, so its stage is 32 KB and six stages fit.
+template <int CG>
+struct Ring {
+  static constexpr int B_ROWS = BN / CG;
+  static constexpr int B_BYTES = B_ROWS * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = CG == 1 ? 4 : 6;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
+};
 constexpr int EPI_WARPS = 16;                    // four warps per TMEM lane quarter
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int NUM_THREADS = 64 + EPI_THREADS;    // TMA warp, MMA warp, epilogue warps
@@ -72,15 +91,15 @@ constexpr uint32_t ACC_COLS = 256;               // one 128 x 256 FP32 accumulat
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;     // two chunk buffers
 constexpr int COL_GROUPS = EPI_WARPS / 4;        // column groups of a tile
 constexpr int TCOLS = BN / COL_GROUPS;            // columns per epilogue thread
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
 constexpr unsigned long long DRAIN_NS = 200000000ull;
 
 // Instruction descriptor, kind::f16: D=F32 (bits 4-5 = 1), A and B format at
 // bits 7-9 / 10-12 (BF16 = 1, F16 = 0; always the same for A and B), both
-// K-major (bits 15,16 = 0), N>>3 at bit 17, M>>4 at bit 24.
-constexpr uint32_t idesc_for(bool f16) {
+// K-major (bits 15,16 = 0), N>>3 at bit 17, M>>4 at bit 24. M is the rows of
+// one instruction: BM, or 2 BM for a CTA pair.
+constexpr uint32_t idesc_for(bool f16, int m) {
   return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -107,25 +126,39 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// CL: acquire at cluster scope, for barriers that the peer CTA of a pair arrives
+// on (or that its tensor-core operations signal)
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if constexpr (CL) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
   return ok != 0;
 }
 
 // Wait for the phase of parity `parity` to complete. Gives up (returning
 // false) when the abort flag is raised or after limit_ns, raising the flag.
+template <bool CL = false>
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag,
                           unsigned long long limit_ns) {
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait<CL>(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*((volatile int*)abort_flag)) return false;
       if (globaltimer() - t0 > limit_ns) {
@@ -141,6 +174,41 @@ __device__ void mbar_wait_drain(uint64_t* bar, uint32_t parity, unsigned long lo
   const unsigned long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity))
     if (globaltimer() - t0 > limit_ns) return;
+}
+
+// ---- CTA pairs (cluster of two; rank 0 issues the copies and the MMAs)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t rank) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(addr), "r"(rank));
+  return d;
+}
+
+// every thread of both CTAs (barrier initialisation and TMEM ownership before,
+// shared-memory and TMEM lifetime after the work)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Arrive on a barrier of the peer CTA. Relaxed for the drained-TMEM signal: the
+// waiter relies only on this thread's TMEM reads being done, which
+// tcgen05.wait::ld already guarantees in program order (a release would first
+// wait for every global store of the tile-end epilogue to become visible
+// cluster-wide). Release for the relayed stage-ready signal, which passes on the
+// visibility of the TMA writes this thread has just observed.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster_release(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst,
@@ -172,19 +240,49 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   return d;
 }
 
+// CG = 2: one instruction of M = 256 over the CTA pair. A's rows 0-127 and B's
+// columns 0-127 come from this CTA's shared memory, A's rows 128-255 and B's
+// columns 128-255 from the same offsets in the peer's; D rows 0-127 land in this
+// CTA's TMEM, rows 128-255 in the peer's, at the same address.
+template <int CG>
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  if constexpr (CG == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
 }
 
+// arrive on `bar` of this CTA once the tensor-core operations issued so far are done
+template <int CG>
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  if constexpr (CG == 2)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// the same, arriving on the barrier at this offset in both CTAs of the pair
+__device__ __forceinline__ void umma_commit_both(uint64_t* bar) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"((uint16_t)3)
       : "memory");
 }
 
@@ -227,25 +325,24 @@ constexpr int KIND_BF16X2 = 0, KIND_FP16X2 = 1, KIND_BF16X3 = 2;
 // plane indices of an operand: 0 = hi, 1 = lo, 2 = mid (BF16X3)
 constexpr int PL_HI = 0, PL_LO = 1, PL_MID = 2;
 
-// planes of the left and right factor in base segment `seg` (K-concatenated
-// split product), and the weight of that segment's chunks
+// Planes of the left and right factor in base segment `seg` of a split product
+// of nbase segments (K-concatenated), smallest terms first and hi*hi last: the
+// FP32 register sum then adds terms in increasing size, and a tile starts with
+// the long cross-term chunks, which is what the spare TMEM buffer overlaps with
+// the previous tile's stores. nbase == 1 (split-tail bulk): hi*hi alone.
 template <int KIND>
-__device__ __forceinline__ void seg_planes(int seg, int& pa, int& pb) {
-  if constexpr (KIND == KIND_BF16X3) {
-    // hh, hm, mh, hl, mm, lh
-    pa = (seg == 2 || seg == 4) ? PL_MID : (seg == 5 ? PL_LO : PL_HI);
-    pb = (seg == 1 || seg == 4) ? PL_MID : (seg == 3 ? PL_LO : PL_HI);
+__device__ __forceinline__ void seg_planes(int seg, int nbase, int& pa, int& pb) {
+  if (seg == nbase - 1) {
+    pa = pb = PL_HI;
+  } else if constexpr (KIND == KIND_BF16X3) {
+    // lh, mm, hl (2^-16 of hh), mh, hm (2^-8), then hh
+    pa = seg == 0 ? PL_LO : ((seg == 1 || seg == 3) ? PL_MID : PL_HI);
+    pb = seg == 2 ? PL_LO : ((seg == 1 || seg == 4) ? PL_MID : PL_HI);
   } else {
-    // hh, hl, lh
-    pa = seg == 2 ? PL_LO : PL_HI;
-    pb = seg == 1 ? PL_LO : PL_HI;
+    // hl, lh, then hh
+    pa = seg == 1 ? PL_LO : PL_HI;
+    pb = seg == 0 ? PL_LO : PL_HI;
   }
-}
-
-template <int KIND>
-__device__ __forceinline__ float seg_weight(int seg) {
-  if constexpr (KIND == KIND_FP16X2) return seg == 0 ? 1.0f : 1.0f / kLoScale;
-  return 1.0f;
 }
 
 template <int KIND>
@@ -274,7 +371,8 @@ __device__ __forceinline__ void store_split(float* m, uint16_t* hi, uint16_t* mi
 
 struct KParams {
   int nkb;                 // k-blocks (of BK) per segment: np / BK
-  int ch;                  // k-blocks per TMEM chunk
+  int ch;                  // k-blocks per TMEM chunk of a product's leading (hi x hi) segment
+  int ch_lo;               // k-blocks per TMEM chunk of its other segments
   int nbase;               // segments of one split product (3, or 6 for BF16X3)
   int nseg;                // segments on the K axis (nbase, or 2 nbase for EPI_SYMM)
   int64_t np;
@@ -298,7 +396,8 @@ struct KParams {
 };
 
 // Tensor maps of one launch: the left factor's planes with 128-row boxes (A role)
-// and the right factor's with 256-row boxes (B role); EPI_SYMM also reads X in
+// and the right factor's with 256-row boxes (B role; 128 rows for a CTA pair,
+// which loads each half separately); EPI_SYMM also reads X in
 // the A role and Y in the B role (its second half, [X | .] . [. ; Y]).
 struct KMaps {
   CUtensorMap pa[3];   // P planes (hi, lo, mid), A role
@@ -308,13 +407,14 @@ struct KMaps {
 };
 
 // The stores and partials of one finished tile: row r of the tile, columns
-// [grp * 64, grp * 64 + 64); acc holds this thread's FP32 sums. The epilogue
+// [grp * 64, grp * 64 + 64); acc holds this thread's FP32 sums; the tile's
+// partials (of this CTA's rows) go to p.part[pidx]. The epilogue
 // is a template parameter, so that each kernel carries only its own code (a
 // smaller kernel keeps the producer's and the MMA issuer's loops in the
 // instruction cache).
 template <int KIND, int EPI>
-__device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], int tix, int it,
-                                         int e, int lane, int grp, int r, int sg,
+__device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], int tix, int pidx,
+                                         int it, int e, int lane, int grp, int r, int sg,
                                          double (*red)[3][EPI_WARPS]) {
   constexpr bool F16 = KIND == KIND_FP16X2;
   constexpr bool X3 = KIND == KIND_BF16X3;
@@ -454,28 +554,34 @@ __device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], 
         s2 += red[pb][1][w];
         s3 += red[pb][2][w];
       }
-      p.part[tix] = Part3{s1, s2, s3};
+      p.part[pidx] = Part3{s1, s2, s3};
     }
   }
 }
 
-template <int KIND, int EPI>
+template <int KIND, int EPI, int CG>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
+  using R = Ring<CG>;
+  constexpr int STAGES = R::STAGES;
+  constexpr int STAGE_BYTES = R::STAGE_BYTES;
+  constexpr bool PAIR = CG == 2;
   constexpr bool F16 = KIND == KIND_FP16X2;
-  constexpr bool X3 = KIND == KIND_BF16X3;
-  constexpr uint32_t kIdesc = idesc_for(F16);
+  constexpr uint32_t kIdesc = idesc_for(F16, BM * CG);
   DevState* st = p.st;
   {
+    // a pair must take this exit together: stop_at is fixed for the launch, while
+    // the abort flag may be raised meanwhile (a pair sees it in its waits instead)
     const int m = *((volatile const int*)&st->stop_at);
-    if ((m != 0 && p.step > m) || *((volatile const int*)&st->abort_flag)) return;
+    if ((m != 0 && p.step > m) || (!PAIR && *((volatile const int*)&st->abort_flag))) return;
   }
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;   // [2] chunk accumulated in TMEM buffer b
+  uint64_t* pfull = empty + STAGES;   // pair, rank 0: the peer's stage s has landed
+  uint64_t* tfull = pfull + STAGES;   // [2] chunk accumulated in TMEM buffer b
   uint64_t* tempty = tfull + 2;       // [2] TMEM buffer b drained by the epilogue warps
   uint64_t* mdone = tempty + 2;       // abort path: the MMA issuer's last operations done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
@@ -483,24 +589,39 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* abortf = &st->abort_flag;
+  // a pair: each CTA loads its own halves of both operands (rows rank*128 .. of the
+  // A tile and of the B tile) and drains its own TMEM rows; rank 0 issues the MMAs
+  // once its own stage and (relayed by rank 1's warp 1) the peer's have landed.
+  // Tiles are indexed per pair.
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool issuer = rank == 0;
+  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   // segments of this launch: the split product, or in the split-tail mode's bulk
   // steps the hi planes alone (one segment; two for the symmetric response)
   const int nbase = (p.tail && st->plane1[p.step]) ? 1 : p.nbase;
   const int nseg = EPI == EPI_SYMM ? 2 * nbase : nbase;
   const int total_kb = nseg * p.nkb;
-  const int nchunks = total_kb / p.ch;
-  // persistent static schedule: this CTA handles tiles blockIdx.x, +gridDim.x, ...
-  const int my_tiles =
-      (int)blockIdx.x < p.ntiles ? (p.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // TMEM chunks: the hi x hi segment of each split product (the last of its
+  // nbase segments; every segment in the split-tail bulk) every ch k-blocks, the
+  // smaller cross terms every ch_lo; both divide nkb, so no chunk spans two segments
+  const int ch_hi = p.ch, ch_lo = nbase == 1 ? p.ch : p.ch_lo;
+  const int nchunks = (nseg / nbase) * (p.nkb / ch_hi + (nbase - 1) * (p.nkb / ch_lo));
+  auto chunk_len = [&](int kb0) {
+    return ((kb0 / p.nkb) % nbase) == nbase - 1 ? ch_hi : ch_lo;
+  };
+  // persistent static schedule: this CTA (pair) handles tiles unit, unit + nunits, ...
+  const int my_tiles = unit < p.ntiles ? (p.ntiles - 1 - unit) / nunits + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&pfull[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], EPI_WARPS);
+      mbar_init(&tempty[b], CG * EPI_WARPS);   // a pair's rank 0 hears both CTAs' warps
     }
     mbar_init(mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -508,14 +629,24 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.qb[0])) : "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    // a pair allocates the same columns in both CTAs, one warp of each taking part
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -527,12 +658,12 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
       int64_t g = 0;
       bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it) {
-        const Tile t = p.tiles[blockIdx.x + it * gridDim.x];
+        const Tile t = p.tiles[unit + it * nunits];
         const int bat = (int)(t.row0 / np);
         for (int kb = 0; kb < total_kb; ++kb, ++g) {
           const int s = (int)(g % STAGES);
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
+          if (!mbar_wait<PAIR>(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -541,11 +672,13 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
           const int kx = (kb - seg * nkb) * BK;
           const bool swap = EPI == EPI_SYMM && seg >= nbase;   // second half: [Q | .] . [. ; P]
           int pa, pb;
-          seg_planes<KIND>(swap ? seg - nbase : seg, pa, pb);
+          seg_planes<KIND>(swap ? seg - nbase : seg, nbase, pa, pb);
           const CUtensorMap* ma = swap ? &maps.qa[pa] : &maps.pa[pa];
           const CUtensorMap* mb = swap ? &maps.pb[pb] : &maps.qb[pb];
-          const int arow = swap ? t.row0 - bat * (int)np : t.row0;
-          const int brow = swap ? bat * (int)np + t.col0 : t.col0;
+          // this CTA's halves: rows [rank*128, +128) of the A tile, [rank*B_ROWS, +B_ROWS)
+          // of the B tile (one CTA: all of both)
+          const int arow = (swap ? t.row0 - bat * (int)np : t.row0) + (int)rank * BM;
+          const int brow = (swap ? bat * (int)np + t.col0 : t.col0) + (int)rank * R::B_ROWS;
           uint8_t* sa = smem + s * STAGE_BYTES;
           mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
           tma_load_2d(ma, &full[s], sa, kx, arow);
@@ -562,24 +695,35 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      const int ch = p.ch;
+    if (PAIR && !issuer && lane == 0) {
+      // rank 1: pass each landed stage of this CTA on to rank 0's MMA issuer
+      const uint32_t pfull_peer = cluster_addr(smem_u32(pfull), 0);
+      const int64_t total = (int64_t)my_tiles * total_kb;
+      for (int64_t g = 0; g < total; ++g) {
+        const int s = (int)(g % STAGES);
+        if (!mbar_wait<PAIR>(&full[s], (uint32_t)(g / STAGES) & 1u, abortf, p.wait_ns)) break;
+        mbar_arrive_cluster_release(pfull_peer + (uint32_t)(s * sizeof(uint64_t)));
+      }
+    } else if (lane == 0 && issuer) {
       bool ok = true;
       int64_t g = 0, gc = 0;   // k-block and chunk counters across tiles
       for (int it = 0; it < my_tiles && ok; ++it) {
+        int kb0 = 0;   // first k-block of chunk c within the tile
         for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+          const int len = chunk_len(kb0);
           const int b = (int)(gc & 1);
-          // the epilogue has drained buffer b (chunk gc-2)
-          if (!mbar_wait(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf, p.wait_ns)) {
+          // the epilogue (of both CTAs of a pair) has drained buffer b (chunk gc-2)
+          if (!mbar_wait<PAIR>(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf, p.wait_ns)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
-          for (int kb = c * ch; kb < (c + 1) * ch; ++kb, ++g) {
+          for (int kb = kb0; kb < kb0 + len; ++kb, ++g) {
             const int s = (int)(g % STAGES);
             const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, abortf, p.wait_ns)) {
+            if (!mbar_wait<PAIR>(&full[s], ph, abortf, p.wait_ns) ||
+                (PAIR && !mbar_wait<PAIR>(&pfull[s], ph, abortf, p.wait_ns))) {
               ok = false;
               break;
             }
@@ -590,18 +734,24 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
               // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
-              umma_f16(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
-                       (kb > c * ch || k > 0) ? 1u : 0u);
+              umma_f16<CG>(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                           (kb > kb0 || k > 0) ? 1u : 0u);
             }
-            umma_commit(&empty[s]);
+            // the stage is free in both CTAs once these MMAs have read it
+            if constexpr (PAIR) umma_commit_both(&empty[s]);
+            else umma_commit<CG>(&empty[s]);
           }
-          if (ok) umma_commit(&tfull[b]);
+          if (ok) {
+            if constexpr (PAIR) umma_commit_both(&tfull[b]);
+            else umma_commit<CG>(&tfull[b]);
+          }
+          kb0 += len;
         }
       }
       if (!ok) {
         // aborted: the tensor-core operations already issued still read the ring and
         // write TMEM; one more commit tracks all of them (bounded wait) before dealloc
-        umma_commit(mdone);
+        umma_commit<CG>(mdone);
         mbar_wait_drain(mdone, 0, DRAIN_NS);
       }
     }
@@ -615,8 +765,10 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
     const int e = warp - 2;
     const int q = warp & 3;
     const int grp = e >> 2;
-    const int r = q * 32 + lane;
+    const int r = (int)rank * BM + q * 32 + lane;   // row within the (pair) tile
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(grp * TCOLS);
+    // a pair's rank 1 reports drained buffers to rank 0's barrier
+    const uint32_t tempty_peer = PAIR && !issuer ? cluster_addr(smem_u32(tempty), 0) : 0u;
     // the branch of this step (uniform over the launch); the previous iterate is
     // read by the square and, for sigma < 0, by the response update
     const int sg = EPI == EPI_PLAIN ? 1 : p.st->sigma[p.step];
@@ -624,7 +776,7 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
     bool ok = true;
     int64_t gc = 0;
     for (int it = 0; it < my_tiles && ok; ++it) {
-      const int tix = blockIdx.x + it * gridDim.x;
+      const int tix = unit + it * nunits;
       // the previous-iterate entries the tile-end epilogue reads (256 B of this
       // thread's row), pulled into L2 two chunks ahead of the tile's end
       const float* pf = nullptr;
@@ -635,9 +787,12 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
       float acc[TCOLS];
 #pragma unroll
       for (int j = 0; j < TCOLS; ++j) acc[j] = 0.0f;
+      int kb0 = 0;
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int b = (int)(gc & 1);
-        bool w = mbar_wait(&tfull[b], (uint32_t)(gc >> 1) & 1u, abortf, p.wait_ns);
+        const int seg = kb0 / p.nkb;
+        kb0 += chunk_len(kb0);
+        bool w = mbar_wait<PAIR>(&tfull[b], (uint32_t)(gc >> 1) & 1u, abortf, p.wait_ns);
         w = __all_sync(0xffffffffu, w);
         if (!w) {
           ok = false;
@@ -649,7 +804,7 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
                        "r"((uint32_t)(TCOLS * sizeof(float)))
                        : "memory");
         float wgt = 1.0f;
-        if constexpr (F16) wgt = (((c * p.ch) / p.nkb) % nbase) == 0 ? 1.0f : 1.0f / kLoScale;
+        if constexpr (F16) wgt = (seg % nbase) == nbase - 1 ? 1.0f : 1.0f / kLoScale;
 #pragma unroll
         for (int c0 = 0; c0 < TCOLS; c0 += 16) {
           uint32_t v[16];
@@ -659,21 +814,34 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[b]);
+        if (lane == 0) {
+          if (PAIR && !issuer)
+            mbar_arrive_cluster(tempty_peer + (uint32_t)(b * sizeof(uint64_t)));
+          else
+            mbar_arrive(&tempty[b]);
+        }
       }
       if (!ok || *((volatile int*)abortf)) break;
-      tile_end<KIND, EPI>(p, acc, tix, it, e, lane, grp, r, sg, red);
+      tile_end<KIND, EPI>(p, acc, tix, tix * CG + (int)rank, it, e, lane, grp, r, sg, red);
     }
   }
 
+  // a CTA (pair) leaves only when every copy into its shared memory and every
+  // tensor-core operation on its TMEM is done or drained above
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
-                 : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(TMEM_COLS)
+                   : "memory");
   }
 }
 
@@ -710,43 +878,82 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int bo
   return r == CUDA_SUCCESS;
 }
 
-// one launch of the (KIND, EPI) kernel, with its shared-memory attribute set once
-template <int KIND, int EPI>
-cudaError_t launch_kind(const KMaps& maps, const KParams& p, int grid, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<KIND, EPI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+// one launch of the (KIND, EPI, CG) kernel over `units` CTAs or CTA pairs (at most
+// the resident ones), with its shared-memory attribute and its resident-pair
+// count queried once
+template <int KIND, int EPI, int CG>
+cudaError_t launch_kind(const KMaps& maps, const KParams& p, int units, cudaStream_t s) {
+  static int resident = 0;
+  auto kern = k_gemm_tc<KIND, EPI, CG>;
+  constexpr int smem = Ring<CG>::SMEM_BYTES;
+  if (!resident) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (CG == 1) {
+      resident = nsm;   // one CTA per SM: the ring leaves no room for a second
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CG;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(CG * (nsm / CG)));
+      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      e = cudaOccupancyMaxActiveClusters(&nc, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      if (nc < 1) return cudaErrorNotSupported;
+      resident = nc;
+    }
   }
-  k_gemm_tc<KIND, EPI><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(maps, p);
-  return cudaGetLastError();
+  const int n = units < resident ? units : resident;
+  if (CG == 1) {
+    kern<<<n, NUM_THREADS, smem, s>>>(maps, p);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CG;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(CG * n));
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, maps, p);
 }
 
-template <int KIND>
-cudaError_t launch_epi(int epi, const KMaps& maps, const KParams& p, int grid, cudaStream_t s) {
-  if (epi == EPI_SQUARE) return launch_kind<KIND, EPI_SQUARE>(maps, p, grid, s);
-  if (epi == EPI_SYMM) return launch_kind<KIND, EPI_SYMM>(maps, p, grid, s);
-  return launch_kind<KIND, EPI_PLAIN>(maps, p, grid, s);
+template <int KIND, int CG>
+cudaError_t launch_epi(int epi, const KMaps& maps, const KParams& p, int units, cudaStream_t s) {
+  if (epi == EPI_SQUARE) return launch_kind<KIND, EPI_SQUARE, CG>(maps, p, units, s);
+  if (epi == EPI_SYMM) return launch_kind<KIND, EPI_SYMM, CG>(maps, p, units, s);
+  return launch_kind<KIND, EPI_PLAIN, CG>(maps, p, units, s);
+}
+
+template <int CG>
+cudaError_t launch_cg(int kind, int epi, const KMaps& maps, const KParams& p, int units,
+                      cudaStream_t s) {
+  if (kind == KIND_FP16X2) return launch_epi<KIND_FP16X2, CG>(epi, maps, p, units, s);
+  if (kind == KIND_BF16X3) return launch_epi<KIND_BF16X3, CG>(epi, maps, p, units, s);
+  return launch_epi<KIND_BF16X2, CG>(epi, maps, p, units, s);
 }
 
 }  // namespace
 
-void tc_tile_shape(int* bm, int* bn) {
-  *bm = BM;
+void tc_tile_shape(int pair, int* bm, int* bn) {
+  *bm = pair ? 2 * BM : BM;
   *bn = BN;
-}
-
-int tc_grid(int ntiles) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      nsm = 1;
-  }
-  return ntiles < nsm ? ntiles : nsm;
 }
 
 cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size_t errlen) {
@@ -755,6 +962,7 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   const int kind = mode == SP2_MODE_FP16X2 ? KIND_FP16X2
                                            : (mode == SP2_MODE_BF16X3 ? KIND_BF16X3 : KIND_BF16X2);
   const bool f16 = kind == KIND_FP16X2, x3 = kind == KIND_BF16X3;
+  const int cg = L.tune.pair ? 2 : 1;   // the tile list was built for this tile shape
   const TcOperand& P = L.P;
   const TcOperand& Q = L.Q;
   // the middle planes exist only in BF16X3; elsewhere the hi maps stand in (never read)
@@ -775,7 +983,7 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   if ((reinterpret_cast<uintptr_t>(P.hi) | reinterpret_cast<uintptr_t>(P.lo) |
        reinterpret_cast<uintptr_t>(Q.hi) | reinterpret_cast<uintptr_t>(Q.lo) |
        reinterpret_cast<uintptr_t>(p_mid) | reinterpret_cast<uintptr_t>(q_mid)) & 15u ||
-      np % 256 != 0 || P.rows % np != 0 || Q.rows % np != 0 || P.rows % BM != 0 ||
+      np % 256 != 0 || P.rows % np != 0 || Q.rows % np != 0 || P.rows % (BM * cg) != 0 ||
       Q.rows % BN != 0 || (L.epi == EPI_SYMM && Q.rows != np) ||
       (L.epi == EPI_SQUARE && P.rows != np) || P.rows > (int64_t)1 << 30) {
     snprintf(errbuf, errlen, "tcgen05 product: operand alignment/shape violates the TMA rules");
@@ -787,10 +995,10 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   bool mapped = true;
   for (int i = 0; i < 3; ++i) {
     mapped = mapped && make_map(&maps.pa[i], pp[i], P.rows, np, BM, f16) &&
-             make_map(&maps.qb[i], qq[i], Q.rows, np, BN, f16);
+             make_map(&maps.qb[i], qq[i], Q.rows, np, BN / cg, f16);
     // EPI_SYMM's second half reads X as the left and Y as the right factor
     mapped = mapped && make_map(&maps.qa[i], qq[i], Q.rows, np, BM, f16) &&
-             make_map(&maps.pb[i], pp[i], P.rows, np, BN, f16);
+             make_map(&maps.pb[i], pp[i], P.rows, np, BN / cg, f16);
   }
   if (!mapped) {
     snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
@@ -806,6 +1014,12 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   // exact form, 512-wide 2.5e-5 and 2048-wide 7.6e-4, for 3% more time per
   // product than 512-wide chunks.
   p.ch = 4;
+  // The cross terms (hi*lo, lo*hi; in BF16X3 everything after hi*hi) are at most
+  // 2^-8 of the leading term once weighted, so the truncation bias of a longer
+  // TMEM accumulation shrinks with them: up to 2048-wide chunks (32 k-blocks,
+  // the largest power of two up to 32 that divides np / BK).
+  p.ch_lo = 32;
+  while ((np / BK) % p.ch_lo != 0) p.ch_lo >>= 1;
   p.nbase = x3 ? 6 : 3;
   p.nseg = L.epi == EPI_SYMM ? 2 * p.nbase : p.nbase;
   p.np = np;
@@ -827,10 +1041,9 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   p.withhold = L.tune.withhold;
   p.tail = L.tail;
   // persistent: one CTA per SM (the shared-memory ring allows no second one)
-  const int grid = tc_grid(L.ntiles);
-  if (kind == KIND_FP16X2) return launch_epi<KIND_FP16X2>(L.epi, maps, p, grid, s);
-  if (kind == KIND_BF16X3) return launch_epi<KIND_BF16X3>(L.epi, maps, p, grid, s);
-  return launch_epi<KIND_BF16X2>(L.epi, maps, p, grid, s);
+  // persistent: one CTA (pair) per SM (pair of SMs), the launch's tiles spread over them
+  if (cg == 2) return launch_cg<2>(kind, L.epi, maps, p, L.ntiles, s);
+  return launch_cg<1>(kind, L.epi, maps, p, L.ntiles, s);
 }
 
 }  // namespace sp2

@@ -516,7 +516,7 @@ __global__ void k_split_scaled(MatBuf m, int64_t per, ScaleBuf sc, int slot) {
 // with the spectrum of X in [0, 1]; either way ||Y_{n+1}||_2 <= 2 ||Y_n||_2,
 // and |entry| <= 2-norm <= Frobenius norm. The plane scale of Y_{n+2} is
 // therefore fixed by ||Y_{n+1}||_F before the step that writes it.
-__global__ void k_sym_scale(const Part3* part, const Tile* tiles, int ntiles, int64_t np,
+__global__ void k_sym_scale(const Part3* part, int ppt, const Tile* tiles, int ntiles, int64_t np,
                             const DevState* st, int step, float* scale_out) {
   if (st) {
     const int m = st->stop_at;
@@ -525,7 +525,8 @@ __global__ void k_sym_scale(const Part3* part, const Tile* tiles, int ntiles, in
   const int64_t b = blockIdx.x;
   double acc = 0.0;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-    if (tiles[t].row0 / np == b) acc += part[t].t2;
+    if (tiles[t].row0 / np == b)
+      for (int j = 0; j < ppt; ++j) acc += part[t * ppt + j].t2;
   acc = block_sum(acc);
   if (threadIdx.x == 0) scale_out[b] = pow2_scale((float)(2.0 * sqrt(fmax(acc, 0.0))));
 }
@@ -760,10 +761,11 @@ cudaError_t launch_split_scaled(MatBuf m, int64_t np, ScaleBuf sc, int slot, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_sym_scale(const Part3* part, const Tile* tiles, int ntiles, int64_t np,
+cudaError_t launch_sym_scale(const Part3* part, int ppt, const Tile* tiles, int ntiles, int64_t np,
                              int64_t batch, const DevState* st, int step, float* scale_out,
                              cudaStream_t s) {
-  k_sym_scale<<<(unsigned)batch, kRedThreads, 0, s>>>(part, tiles, ntiles, np, st, step, scale_out);
+  k_sym_scale<<<(unsigned)batch, kRedThreads, 0, s>>>(part, ppt, tiles, ntiles, np, st, step,
+                                                        scale_out);
   return cudaGetLastError();
 }
 

@@ -236,10 +236,13 @@ int join_beside(sp2_handle_t h) {
 size_t dsize(int dtype) { return dtype == SP2_F64 ? 8 : 4; }
 
 // --------------------------------------------------------------- tile lists
-void tile_shape(int mode, int* bm, int* bn) {
-  if (split_mode(mode)) tc_tile_shape(bm, bn);
+void tile_shape(sp2_handle_t h, int mode, int* bm, int* bn) {
+  if (split_mode(mode)) tc_tile_shape(h->tune.pair, bm, bn);
   else simt_tile_shape(mode, bm, bn);
 }
+
+// partials per output tile: a CTA pair's two CTAs each report their own rows
+int parts_per_tile(sp2_handle_t h, int mode) { return split_mode(mode) && h->tune.pair ? 2 : 1; }
 
 // Output tiles of a (rows x np) product in an L2-friendly order: groups of 8
 // row blocks sweep the column blocks together, so CTAs resident at the same
@@ -248,9 +251,10 @@ void tile_shape(int mode, int* bm, int* bn) {
 int tile_list(sp2_handle_t h, int mode, int64_t rows, int64_t np, bool upper, const Tile** d,
               int* n) {
   int bm, bn;
-  tile_shape(mode, &bm, &bn);
+  tile_shape(h, mode, &bm, &bn);
   char key[96];
-  snprintf(key, sizeof key, "%d/%lld/%lld/%d", mode, (long long)rows, (long long)np, (int)upper);
+  snprintf(key, sizeof key, "%d/%lld/%lld/%d/%dx%d", mode, (long long)rows, (long long)np,
+           (int)upper, bm, bn);
   auto it = h->tiles.find(key);
   if (it != h->tiles.end()) {
     *d = it->second.d;
@@ -351,7 +355,7 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   int nt;
   TRY(tile_list(h, c.mode, c.np, c.np, true, &tl, &nt));
   int bm, bn;
-  tile_shape(c.mode, &bm, &bn);
+  tile_shape(h, c.mode, &bm, &bn);
   TcLaunch L;   // workspace first: nothing is allocated inside the timed interval
   if (split_mode(c.mode)) TRY(tc_common(c, &L, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -382,7 +386,7 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   c.kernels++;
   c.flops += 2.0 * bm * bn * (double)c.np * k_mult(c.mode) * nt;
   c.alg += (double)c.n * (double)(c.n + 1) * (double)c.n * k_mult(c.mode);
-  *nparts = nt;
+  *nparts = nt * parts_per_tile(h, c.mode);
   return SP2_OK;
 }
 
@@ -403,13 +407,13 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
   int nt;
   TRY(tile_list(h, c.mode, rows, c.np, fused, &tl, &nt));
   int bm, bn;
-  tile_shape(c.mode, &bm, &bn);
+  tile_shape(h, c.mode, &bm, &bn);
   // workspace first: nothing is allocated inside the timed interval
   TcLaunch L;
   void* yp = nullptr;
   void* z = nullptr;
   if (fused) {
-    TRY(ws(h, "ypart", (size_t)nt * sizeof(Part3), &yp));
+    TRY(ws(h, "ypart", (size_t)nt * parts_per_tile(h, c.mode) * sizeof(Part3), &yp));
   } else {
     TRY(ws(h, "Z", (size_t)rows * c.np * master_size(c.mode), &z));
   }
@@ -441,7 +445,8 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
       c.timed.push_back({step, 0});
     }
     if (f16) {
-      CK(launch_sym_scale(static_cast<Part3*>(yp), tl, nt, c.np, batch, c.st, step,
+      CK(launch_sym_scale(static_cast<Part3*>(yp), parts_per_tile(h, c.mode), tl, nt, c.np, batch,
+                          c.st, step,
                           sc.yscale + slot_in * sc.B, h->stream));
       c.kernels++;
     }
@@ -808,8 +813,8 @@ int make_ctx(sp2_handle_t h, int mode, int64_t n, int64_t np, bool timing, Ctx* 
   c->timing = timing;
   c->st = h->d_state;
   int bm, bn;
-  tile_shape(mode, &bm, &bn);
-  int64_t maxp = (np / bm) * (np / bn) + 8;
+  tile_shape(h, mode, &bm, &bn);
+  int64_t maxp = (np / bm) * (np / bn) * parts_per_tile(h, mode) + 8;
   if (maxp < init_nparts(np)) maxp = init_nparts(np);
   void* p;
   TRY(ws(h, "part", (size_t)maxp * sizeof(Part3), &p));
@@ -1061,7 +1066,7 @@ int fprod(Ctx& c, FMat& C, const FMat& L, const FMat& R) {
   int nt;
   TRY(tile_list(h, c.mode, c.np, c.np, false, &tl, &nt));
   int bm, bn;
-  tile_shape(c.mode, &bm, &bn);
+  tile_shape(h, c.mode, &bm, &bn);
   TcLaunch T;   // workspace first: nothing is allocated inside the timed interval
   if (split_mode(c.mode)) TRY(tc_common(c, &T, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1234,6 +1239,9 @@ int sp2_set_option(sp2_handle_t h, int option, int64_t value) {
       return SP2_OK;
     case SP2_OPTION_FUSED_RESPONSE:
       h->tune.fused_response = value != 0 ? 1 : 0;
+      return SP2_OK;
+    case SP2_OPTION_PAIR_TILES:
+      h->tune.pair = value != 0 ? 1 : 0;
       return SP2_OK;
     default:
       return fail(h, SP2_EINVAL, "unknown option %d", option);

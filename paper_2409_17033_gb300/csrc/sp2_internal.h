@@ -216,6 +216,7 @@ struct TcTuning {
   unsigned long long wait_ns = 2000000000ull;  // limit of every mbarrier wait
   int withhold = 0;    // test hook: the first TMA load of CTA 0 is never issued
   int fused_response = 0;  // response step as one EPI_SYMM launch (else EPI_PLAIN + transpose-add)
+  int pair = 1;        // 256 x 256 tiles on CTA pairs (tcgen05 cta_group::2), else 128 x 256
 };
 // (TcLaunch.tail: the split-tail mode; the kernel reads st->plane1[step] and uses
 // the hi planes alone, one product per segment pair, where it is set.)
@@ -241,14 +242,13 @@ struct TcLaunch {
   TcTuning tune;
 };
 cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size_t errlen);
-void tc_tile_shape(int* bm, int* bn);
-int tc_grid(int ntiles);            // CTAs of a launch over ntiles tiles
+void tc_tile_shape(int pair, int* bm, int* bn);   // output tile of one CTA (pair)
 
 // FP16X2 scale of the next symmetric response step: per batch entry, the sum of
 // the EPI_SYMM tile partials (||Y_{n+1}||_F^2) and the plane scale of Y_{n+2},
 // pow2_scale(2 ||Y_{n+1}||_F) (|Y_{n+2}|_max <= ||Y_{n+2}||_2 <= 2 ||Y_{n+1}||_2).
 // No-op when the recursion stopped before `step`.
-cudaError_t launch_sym_scale(const Part3* part, const Tile* tiles, int ntiles, int64_t np,
+cudaError_t launch_sym_scale(const Part3* part, int ppt, const Tile* tiles, int ntiles, int64_t np,
                              int64_t batch, const DevState* st, int step, float* scale_out,
                              cudaStream_t s);
 // FP16X2: the same bound from a batch's masters (the first response step)
