@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the accuracy report against the FP64 closed forms (host LAPACK)")
     ap.add_argument("--workload", default="chi",
-                    choices=["chi", "fermi", "scf", "nonorth", "configs"])
+                    choices=["chi", "fermi", "scf", "nonorth", "configs", "products"])
+    ap.add_argument("--tiles", default="pair", choices=["pair", "single"],
+                    help="product tiles: 256x256 on CTA pairs, or 128x256 on one SM")
     ap.add_argument("--scf-tol", type=float, default=1e-6)
     return ap.parse_args()
 
@@ -371,6 +373,59 @@ def run_ours(args, ws, rank):
         "clocks": clocks,
     }
 
+    # end to end through the C ABI with host buffers (pinned), copies timed; right
+    # after the device-resident timing, so that both see the same thermal state
+    if not args.no_e2e:
+        Hh = torch.from_numpy(tb.H).pin_memory().numpy()
+        Ah = torch.from_numpy(A).pin_memory().numpy()
+        hh = sp2.Handle()
+        kwh = dict(kw)
+        kwh["handle"] = hh
+        # page-locked result buffers, as a user streaming results to the host would pass
+        kwh["out"] = torch.empty((1, n, n), dtype=torch.float32).pin_memory().numpy()
+        kwh["D_out"] = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
+        sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
+        barrier(ws)
+        ev = [_events() for _ in range(args.steps)]
+        clk_e = ClockSampler(clk.gpu_id)
+        clk_e.start()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            chi_h, D_h, _ = sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        clocks_e = clk_e.stop()
+        e2e_gpu_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        e2e_s = allmax(ws, e2e_s)
+        # raw page-locked copy rates on this box (torch pinned tensors), for reading
+        # the end-to-end overhead
+        scratch = torch.empty_like(H)
+        hpin = torch.empty(H.shape, dtype=H.dtype).pin_memory()
+        torch.cuda.synchronize()
+        c0, c1 = _events()
+        c0.record(stream)
+        scratch.copy_(hpin, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms = c0.elapsed_time(c1)
+        c0.record(stream)
+        hpin.copy_(scratch, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        d2h_ms = c0.elapsed_time(c1)
+        del scratch, hpin
+        line["e2e"] = {"value": whole_job_tflops(ws, lflops, e2e_s * 1e3), "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": int(Hh.nbytes + Ah.nbytes),
+                       "d2h_bytes_per_step": int(chi_h.nbytes + D_h.nbytes),
+                       "ms_per_step": e2e_s * 1e3,
+                       "gpu_ms_per_step": e2e_gpu_ms,
+                       "clocks": clocks_e,
+                       "pinned_copy_gbs": {"h2d": Hh.nbytes / (h2d_ms * 1e-3) / 1e9,
+                                           "d2h": D_h.nbytes / (d2h_ms * 1e-3) / 1e9}}
+        del hh
+
     # plain forms on the same GPU: per-product timings of the FP32 CUDA-core
     # kernels extrapolated to this solve's product count (stated as such)
     if not args.no_plain and rank == 0:
@@ -434,53 +489,6 @@ def run_ours(args, ws, rank):
         except Exception as ex:
             line["history_resident"] = {"error": str(ex)}
 
-    # end to end through the C ABI with host buffers (pinned), copies timed
-    if not args.no_e2e:
-        Hh = torch.from_numpy(tb.H).pin_memory().numpy()
-        Ah = torch.from_numpy(A).pin_memory().numpy()
-        hh = sp2.Handle()
-        kwh = dict(kw)
-        kwh["handle"] = hh
-        # page-locked result buffers, as a user streaming results to the host would pass
-        kwh["out"] = torch.empty((1, n, n), dtype=torch.float32).pin_memory().numpy()
-        kwh["D_out"] = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
-        sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
-        barrier(ws)
-        ev = [_events() for _ in range(args.steps)]
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            chi_h, D_h, _ = sp2.sp2_susceptibility(Hh, tb.nocc, Ah, **kwh)
-            ev[i][1].record(stream)
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        torch.cuda.synchronize()
-        e2e_gpu_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-        e2e_s = allmax(ws, e2e_s)
-        # raw page-locked copy rates on this box (torch pinned tensors), for reading
-        # the end-to-end overhead
-        scratch = torch.empty_like(H)
-        hpin = torch.empty(H.shape, dtype=H.dtype).pin_memory()
-        torch.cuda.synchronize()
-        c0, c1 = _events()
-        c0.record(stream)
-        scratch.copy_(hpin, non_blocking=True)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        h2d_ms = c0.elapsed_time(c1)
-        c0.record(stream)
-        hpin.copy_(scratch, non_blocking=True)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        d2h_ms = c0.elapsed_time(c1)
-        del scratch, hpin
-        line["e2e"] = {"value": whole_job_tflops(ws, lflops, e2e_s * 1e3), "unit": "TFLOP/s",
-                       "h2d_bytes_per_step": int(Hh.nbytes + Ah.nbytes),
-                       "d2h_bytes_per_step": int(chi_h.nbytes + D_h.nbytes),
-                       "ms_per_step": e2e_s * 1e3,
-                       "gpu_ms_per_step": e2e_gpu_ms,
-                       "pinned_copy_gbs": {"h2d": Hh.nbytes / (h2d_ms * 1e-3) / 1e9,
-                                           "d2h": D_h.nbytes / (d2h_ms * 1e-3) / 1e9}}
-        del hh
 
     if rank == 0 and ws == 1 and not args.no_exact:
         # accuracy of this solve against the FP64 closed forms (the oracle leg, host LAPACK);
@@ -774,6 +782,48 @@ def run_nonorth(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_products(args, ws, rank):
+    """The two product kernels alone, for kernel timing and profiling: each step
+    is one forward response step (sigma = +1) of the x-dipole on the N x N
+    tight-binding H (--n, default 16384), i.e. one plain product Y X and one
+    square X^2, in that order, with the tiles of --tiles. Per-launch times are
+    CUDA events around each product launch (the library's time_kernels)."""
+    import numpy as np
+    import torch
+
+    import paper_2409_17033_gb300 as sp2
+    import workloads
+    n = args.n
+    tb = workloads.tight_binding(n, seed=0, dtype=np.float32)
+    H = torch.from_numpy(tb.H).cuda()
+    A = torch.from_numpy(workloads.tb_dipole_observables(tb)[0:1].astype(np.float32)).cuda()
+    h = sp2.Handle()
+    h.set_option("pair_tiles", 1 if args.tiles == "pair" else 0)
+    sq, tot = [], []
+    for i in range(args.warmup + args.steps):
+        _, _, inf = sp2.sp2_susceptibility(H, n // 2, A, "forward", diag_only=True, mode=args.mode,
+                                           sigma=[1], time_kernels=True, handle=h)
+        torch.cuda.synchronize()
+        _, ind = sp2.sp2_density(H, n // 2, mode=args.mode, sigma=[1], time_kernels=True, handle=h)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            tot.append(inf["product_ms"])
+            sq.append(ind["product_ms"])
+    k = {"bf16x3": 6.0, "fp16x2": 3.0, "bf16x2": 3.0}.get(args.mode, 1.0)   # tensor products each
+    sq_ms = float(np.median(sq))
+    pl_ms = float(np.median(tot)) - sq_ms
+    sq_tf = n * (n + 1) * n * k / sq_ms / 1e9
+    pl_tf = 2.0 * n ** 3 * k / pl_ms / 1e9
+    line = {"metric": f"N={n} product kernels: algorithmic TFLOP/s per launch (square X^2, plain Y X)",
+            "value": pl_tf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
+            "config": {"workload": f"tight-binding N={n}, one forward response step (sigma=+1)",
+                       "tiles": args.tiles, "n": n},
+            "square": {"ms": sq_ms, "tflops": sq_tf}, "plain": {"ms": pl_ms, "tflops": pl_tf}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_configs(args, ws, rank):
     """The other configurations of the metric as measurement lines (one GPU):
     config 1, N=128 gapped random spectrum (FP64 to idem_tol 1e-10, and FP16X2):
@@ -909,6 +959,8 @@ def main():
         run_scf(args, ws, rank)
     elif args.workload == "configs":
         run_configs(args, ws, rank)
+    elif args.workload == "products":
+        run_products(args, ws, rank)
     else:
         run_ours(args, ws, rank)
     if ws > 1:
