@@ -30,9 +30,11 @@ Contents (each function cites the passage it follows):
 * ``nonorth``   -- non-orthonormal representations (Sec. V.A): Loewdin factor,
                    congruences, and the dual three-contraction form of the
                    basis-set dependent derivative (Eq. NonOrthDer).
+* ``sparse``    -- Eq. DM0 in blockwise thresholded sparse algebra (Sec. II's
+                   remark on thresholded sparse matrix products).
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 a closed form, an invariant, brute force or a library routine (see
 ``tests/test_oracle_*.py``). None is marked "parity unpinned".
 """
-from . import exact, fermi, nonorth, scf, sp2, split  # noqa: F401
+from . import exact, fermi, nonorth, scf, sp2, sparse, split  # noqa: F401

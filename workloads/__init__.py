@@ -114,7 +114,8 @@ class TightBinding:
 def _tb_hopping(pos: np.ndarray, box: float, rcut: float, decay: float,
                 norb: int, out: np.ndarray) -> None:
     """Adds -exp(-r/decay) to every orbital pair of every pair of distinct
-    sites closer than rcut (minimum-image distance in the periodic cube)."""
+    sites closer than rcut (minimum-image distance in the periodic box; box is
+    the cube edge or the three box edges)."""
     ns = pos.shape[0]
     chunk = 512
     for s0 in range(0, ns, chunk):
@@ -154,6 +155,33 @@ def tight_binding(n: int, seed: int = 0, norb: int = 4, density: float = 0.1,
     _tb_hopping(pos, box, rcut, decay, norb, h)
     h[np.arange(n), np.arange(n)] += eps
     return TightBinding(H=h, pos=pos, box=box, norb=norb, nocc=n // 2)
+
+
+def tight_binding_rod(n: int, seed: int = 0, norb: int = 4, density: float = 0.1,
+                      width: float = 6.0, rcut: float = 6.0, decay: float = 1.5,
+                      onsite: float = 0.3, stagger: float = 2.0,
+                      dtype=np.float64) -> TightBinding:
+    """Dense-stored tight-binding Hamiltonian of a long periodic rod: the stand-in
+    for the large non-metallic systems where thresholded sparse algebra pays.
+
+    n_sites = n / norb sites uniform in [0, L) x [0, width)^2 with
+    L = n_sites / (density * width^2), periodic in all three directions, then
+    sorted by their coordinate along the rod, so that orbital blocks are
+    spatially local. Draw order: positions (n_sites*3 uniforms, row-major,
+    scaled to the box), then onsite energies (n uniforms). Hopping and onsite
+    terms as in tight_binding; the stagger (default 2.0) opens a gap of about
+    0.95 at n = 4096. N_occ = n / 2."""
+    assert n % norb == 0
+    ns = n // norb
+    rng = np.random.default_rng(seed)
+    box = np.array([ns / (density * width * width), width, width])
+    pos = rng.uniform(0.0, 1.0, (ns, 3)) * box
+    pos = pos[np.argsort(pos[:, 0], kind="stable")]
+    eps = rng.uniform(-onsite, onsite, n) + stagger * np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    h = np.zeros((n, n), dtype=dtype)
+    _tb_hopping(pos, box, rcut, decay, norb, h)
+    h[np.arange(n), np.arange(n)] += eps
+    return TightBinding(H=h, pos=pos, box=float(box[0]), norb=norb, nocc=n // 2)
 
 
 def tb_dipole_observables(tb: TightBinding) -> np.ndarray:
