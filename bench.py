@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the accuracy report against the FP64 closed forms (host LAPACK)")
     ap.add_argument("--workload", default="chi",
-                    choices=["chi", "fermi", "scf", "nonorth", "configs", "products"])
+                    choices=["chi", "fermi", "scf", "nonorth", "configs", "products", "sparse"])
+    ap.add_argument("--tau", type=float, default=1e-5, help="block threshold of --workload sparse")
     ap.add_argument("--tiles", default="pair", choices=["pair", "single"],
                     help="product tiles: 256x256 on CTA pairs, or 128x256 on one SM")
     ap.add_argument("--scf-tol", type=float, default=1e-6)
@@ -824,6 +825,65 @@ def run_products(args, ws, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_sparse(args, ws, rank):
+    """Thresholded block-sparse SP2 (Sec. II's thresholded sparse algebra) on the
+    gapped periodic tight-binding rod at N = 8192, 16384 and 32768 (--n caps the
+    largest): per size the dense FP16X2 solve and the block-sparse one at
+    --tau, their times (CUDA events, median of the timed steps), M, the formed
+    share of the upper 256 x 256 blocks, and the relative difference of the two
+    density matrices. The sparse time per N shows the scaling; value is the
+    speedup at the largest N."""
+    import numpy as np
+    import torch
+
+    import paper_2409_17033_gb300 as sp2
+    import workloads
+    stream = torch.cuda.current_stream()
+    h = sp2.Handle()
+    sizes = [n for n in (8192, 16384, 32768) if n <= max(args.n, 8192)]
+    rows = {}
+    for n in sizes:
+        tb = workloads.tight_binding_rod(n, seed=0, dtype=np.float32)
+        H = torch.from_numpy(tb.H).cuda()
+        tb = None
+        res = {}
+        for kind in ("dense", "sparse"):
+            kw = dict(mode=args.mode, handle=h)
+            if kind == "sparse":
+                kw["block_tau"] = args.tau
+            ts = []
+            for i in range(args.warmup + args.steps):
+                e0, e1 = _events()
+                e0.record(stream)
+                D, info = sp2.sp2_density(H, n // 2, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+            res[kind] = (float(np.median(ts)), D, info)
+        dd, ds = res["dense"][1], res["sparse"][1]
+        rows[n] = {"dense_ms": res["dense"][0], "sparse_ms": res["sparse"][0],
+                   "speedup": res["dense"][0] / res["sparse"][0],
+                   "M_dense": res["dense"][2]["M"], "M_sparse": res["sparse"][2]["M"],
+                   "block_fill": res["sparse"][2]["block_fill"],
+                   "rel_diff_D": float(torch.linalg.norm(ds - dd) / torch.linalg.norm(dd)),
+                   "trace_err": abs(res["sparse"][2]["trace"] - n / 2),
+                   "executed_tflops_sparse": res["sparse"][2]["executed_flops"] / (res["sparse"][0] * 1e9)}
+        del H, dd, ds, res
+        torch.cuda.empty_cache()
+    top = sizes[-1]
+    line = {"metric": f"block-sparse SP2 density: speedup over the dense solve at N={top}",
+            "value": rows[top]["speedup"], "unit": "x", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": args.mode,
+            "data": "synthetic",
+            "config": {"workload": "periodic tight-binding rod (density 0.1, width 6, r<6, stagger 2.0), "
+                                   "sites sorted along the rod, N_occ=N/2",
+                       "tau": args.tau, "block": 256, "sizes": sizes},
+            "sizes": {str(k): v for k, v in rows.items()}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_configs(args, ws, rank):
     """The other configurations of the metric as measurement lines (one GPU):
     config 1, N=128 gapped random spectrum (FP64 to idem_tol 1e-10, and FP16X2):
@@ -961,6 +1021,8 @@ def main():
         run_configs(args, ws, rank)
     elif args.workload == "products":
         run_products(args, ws, rank)
+    elif args.workload == "sparse":
+        run_sparse(args, ws, rank)
     else:
         run_ours(args, ws, rank)
     if ws > 1:

@@ -154,6 +154,20 @@ typedef struct {
                           decision is made on the device; the adjoint follows the same steps).
                           With SP2_MODE_BF16X2 this is the bfloat16 bulk / split tail form.
                           0 (default): split products in every step. */
+  int block_sparse;    /* sp2_density, split modes, CTA-pair products (the default), N <= 65536:
+                          != 0 runs Eq. DM0 in thresholded block-sparse algebra (Sec. II's
+                          remark on thresholded sparse matrix products). The iterates are cut
+                          into 256 x 256 blocks; after X_1 and after every step, each
+                          off-diagonal block whose Frobenius norm is <= block_tau is set to
+                          zero (diagonal blocks always stay), and a square forms only the
+                          blocks (I, J) reachable through kept blocks (I, K), (K, J), over those
+                          K alone. block_tau = 0 drops only blocks that are exactly zero (the
+                          dense result, bit for bit, with the zero blocks skipped). The stop
+                          test adds one floor rule: from f <= 1e-4, two steps of opposite
+                          branches that cut f by less than half mark the threshold's floor.
+                          Storage stays dense. 0 (default): the dense recursion. The other
+                          entry points reject != 0. */
+  double block_tau;    /* the block threshold (>= 0, finite) when block_sparse != 0 */
 } sp2_opts;
 
 typedef struct {
@@ -183,6 +197,11 @@ typedef struct {
   int tail_single_steps;              /* split-tail mode: steps 1..M that used the hi planes
                                          alone (executed_flops and algorithmic_flops count
                                          split products for every step) */
+  double block_fill;                  /* block-sparse recursion (block_sparse): mean over steps
+                                         1..M of the share of the upper 256 x 256 blocks each
+                                         square formed (1 = dense); executed_flops and
+                                         algorithmic_flops then count the K blocks the squares
+                                         ran */
 } sp2_info;
 
 typedef struct sp2_handle_s* sp2_handle_t;

@@ -46,6 +46,8 @@ class Opts(C.Structure):
         ("keep_history", C.c_int),
         ("time_kernels", C.c_int),
         ("tail_f", C.c_double),
+        ("block_sparse", C.c_int),
+        ("block_tau", C.c_double),
     ]
 
 
@@ -71,6 +73,7 @@ class Info(C.Structure):
         ("ckpt_k", C.c_int),
         ("refine_iter", C.c_int),
         ("tail_single_steps", C.c_int),
+        ("block_fill", C.c_double),
     ]
 
     def to_dict(self) -> dict:
@@ -96,6 +99,7 @@ class Info(C.Structure):
             "ckpt_k": int(self.ckpt_k),
             "refine_iter": int(self.refine_iter),
             "tail_single_steps": int(self.tail_single_steps),
+            "block_fill": float(self.block_fill),
         }
 
 

@@ -37,11 +37,13 @@ SP2Error = L.SP2Error
 def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: float = -1.0,
               max_iter: int = 0, min_iter: int = -1, sigma=None, bounds=None,
               ckpt_k: int | str = 0, keep_history: bool = False, time_kernels: bool = False,
-              tail_f: float = 0.0):
+              tail_f: float = 0.0, block_tau: float | None = None):
     """sp2_opts with the library defaults for everything not given. Returns
     (opts, keepalive) where keepalive holds the branch array referenced by
     opts.sigma_in. ckpt_k="auto" selects SP2_CKPT_AUTO (keep as much of the
-    X_n history as device memory holds)."""
+    X_n history as device memory holds). block_tau (not None): the
+    thresholded block-sparse recursion with that block threshold
+    (sp2_density only)."""
     lib = L.load()
     o = L.Opts()
     lib.sp2_default_opts(C.byref(o))
@@ -54,6 +56,9 @@ def make_opts(mode: str | int = "bf16x2", idem_tol: float = 0.0, floor_gate: flo
     o.keep_history = 1 if keep_history else 0
     o.time_kernels = 1 if time_kernels else 0
     o.tail_f = float(tail_f)
+    if block_tau is not None:
+        o.block_sparse = 1
+        o.block_tau = float(block_tau)
     keep = None
     if sigma is not None:
         arr = (C.c_int8 * max(1, len(sigma)))(*[int(s) for s in sigma])

@@ -393,6 +393,12 @@ struct KParams {
   unsigned long long wait_ns;
   int withhold;            // test hook: CTA 0 never issues its first load
   int tail;                // split-tail mode: st->plane1[step] selects the hi planes alone
+  // block-sparse square (SPARSE kernels): the tile count, and per tile its listed
+  // 256-wide K blocks klist[tix * nbk .. + kcnt[tix]], all written on the device
+  const int* dyn_ntiles;
+  const int* kcnt;
+  const uint16_t* klist;
+  int nbk;
 };
 
 // Tensor maps of one launch: the left factor's planes with 128-row boxes (A role)
@@ -559,9 +565,27 @@ __device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], 
   }
 }
 
-template <int KIND, int EPI, int CG>
+// Block-sparse squares: the end (exclusive) of the run of listed K blocks that
+// starts at list position q0 and stays inside one dense cross-term chunk (gsz
+// blocks of 256), so that with every block listed the chunks are the dense ones.
+__device__ __forceinline__ int sparse_run_end(const uint16_t* kl, int kc, int gsz, int q0) {
+  const int grp = kl[q0] / gsz;
+  int q1 = q0 + 1;
+  while (q1 < kc && kl[q1] / gsz == grp) ++q1;
+  return q1;
+}
+
+// SPARSE (square on CTA pairs only): the tile list, its length and every tile's
+// K blocks come from the device (the block-sparse plan); a tile's K axis is its
+// listed 256-wide blocks in each segment, hi*hi drained per block and a cross
+// term per run of listed blocks inside one dense 2048-wide chunk, so that with
+// every block listed the chunks, and the results, are the dense kernel's. The
+// sparse loops are separate from the dense ones, which the SPARSE = false
+// kernels alone contain.
+template <int KIND, int EPI, int CG, bool SPARSE = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
+  static_assert(!SPARSE || (EPI == EPI_SQUARE && CG == 2), "block-sparse squares run on pairs");
   using R = Ring<CG>;
   constexpr int STAGES = R::STAGES;
   constexpr int STAGE_BYTES = R::STAGE_BYTES;
@@ -611,7 +635,13 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
     return ((kb0 / p.nkb) % nbase) == nbase - 1 ? ch_hi : ch_lo;
   };
   // persistent static schedule: this CTA (pair) handles tiles unit, unit + nunits, ...
-  const int my_tiles = unit < p.ntiles ? (p.ntiles - 1 - unit) / nunits + 1 : 0;
+  // (block-sparse: the tile count comes from the device)
+  int ntiles = p.ntiles;
+  if constexpr (SPARSE) ntiles = *((volatile const int*)p.dyn_ntiles);
+  const int my_tiles = unit < ntiles ? (ntiles - 1 - unit) / nunits + 1 : 0;
+  // block-sparse: a cross-term chunk is a run of listed K blocks inside one dense
+  // chunk of ch_lo k-blocks (gsz K blocks of 256)
+  const int gsz = p.ch_lo >> 2;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -651,7 +681,44 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
+    if constexpr (SPARSE) {
+     if (lane == 0) {
+      // block-sparse square: every segment walks the tile's listed K blocks
+      int64_t g = 0;
+      bool ok = true;
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        const int tix = unit + it * nunits;
+        const Tile t = p.tiles[tix];
+        const int kc = p.kcnt[tix];
+        const uint16_t* kl = p.klist + (int64_t)tix * p.nbk;
+        for (int seg = 0; seg < nseg && ok; ++seg) {
+          int pa, pb;
+          seg_planes<KIND>(seg, nbase, pa, pb);
+          for (int u = 0; u < 4 * kc; ++u, ++g) {
+            const int s = (int)(g % STAGES);
+            const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+            if (!mbar_wait<PAIR>(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
+              ok = false;
+              break;
+            }
+            if (p.withhold && blockIdx.x == 0 && g == 0) continue;  // test hook: never completes
+            const int kx = (int)kl[u >> 2] * (4 * BK) + (u & 3) * BK;
+            uint8_t* sa = smem + s * STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(&maps.pa[pa], &full[s], sa, kx, t.row0 + (int)rank * BM);
+            tma_load_2d(&maps.qb[pb], &full[s], sa + A_BYTES, kx, t.col0 + (int)rank * R::B_ROWS);
+          }
+        }
+      }
+      if (!ok) {
+        const int64_t first = g > STAGES ? g - STAGES : 0;
+        for (int64_t q = first; q < g; ++q) {
+          if (p.withhold && blockIdx.x == 0 && q == 0) continue;
+          mbar_wait_drain(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, DRAIN_NS);
+        }
+      }
+     }
+    } else if (lane == 0) {
       const int64_t np = p.np;
       const int nkb = p.nkb;
       // k-block counter g runs on across tiles: stage g % STAGES, phase (g / STAGES) & 1
@@ -698,12 +765,63 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
     if (PAIR && !issuer && lane == 0) {
       // rank 1: pass each landed stage of this CTA on to rank 0's MMA issuer
       const uint32_t pfull_peer = cluster_addr(smem_u32(pfull), 0);
-      const int64_t total = (int64_t)my_tiles * total_kb;
+      int64_t total = (int64_t)my_tiles * total_kb;
+      if constexpr (SPARSE) {
+        total = 0;
+        for (int it = 0; it < my_tiles; ++it) total += (int64_t)nseg * 4 * p.kcnt[unit + it * nunits];
+      }
       for (int64_t g = 0; g < total; ++g) {
         const int s = (int)(g % STAGES);
         if (!mbar_wait<PAIR>(&full[s], (uint32_t)(g / STAGES) & 1u, abortf, p.wait_ns)) break;
         mbar_arrive_cluster_release(pfull_peer + (uint32_t)(s * sizeof(uint64_t)));
       }
+    } else if constexpr (SPARSE) {
+     if (lane == 0 && issuer) {
+      bool ok = true;
+      int64_t g = 0, gc = 0;
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        const int tix = unit + it * nunits;
+        const int kc = p.kcnt[tix];
+        const uint16_t* kl = p.klist + (int64_t)tix * p.nbk;
+        for (int seg = 0; seg < nseg && ok; ++seg) {
+          const bool hh = seg == nbase - 1;
+          for (int q0 = 0; q0 < kc && ok; ++gc) {
+            const int q1 = hh ? q0 + 1 : sparse_run_end(kl, kc, gsz, q0);
+            const int b = (int)(gc & 1);
+            if (!mbar_wait<PAIR>(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf, p.wait_ns)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
+            for (int u = 4 * q0; u < 4 * q1; ++u, ++g) {
+              const int s = (int)(g % STAGES);
+              const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+              if (!mbar_wait<PAIR>(&full[s], ph, abortf, p.wait_ns) ||
+                  !mbar_wait<PAIR>(&pfull[s], ph, abortf, p.wait_ns)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+              const uint64_t adesc = sdesc_sw128(a_addr);
+              const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                umma_f16<CG>(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
+                             (u > 4 * q0 || k > 0) ? 1u : 0u);
+              umma_commit_both(&empty[s]);
+            }
+            if (ok) umma_commit_both(&tfull[b]);
+            q0 = q1;
+          }
+        }
+      }
+      if (!ok) {
+        umma_commit<CG>(mdone);
+        mbar_wait_drain(mdone, 0, DRAIN_NS);
+      }
+     }
     } else if (lane == 0 && issuer) {
       bool ok = true;
       int64_t g = 0, gc = 0;   // k-block and chunk counters across tiles
@@ -787,6 +905,53 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
       float acc[TCOLS];
 #pragma unroll
       for (int j = 0; j < TCOLS; ++j) acc[j] = 0.0f;
+      if constexpr (SPARSE) {
+        // the listed K blocks: hi*hi chunks one block each, cross-term chunks by runs
+        const int kc = p.kcnt[tix];
+        const uint16_t* kl = p.klist + (int64_t)tix * p.nbk;
+        int nruns = 0;
+        for (int q0 = 0; q0 < kc; q0 = sparse_run_end(kl, kc, gsz, q0)) ++nruns;
+        const int nch = (nbase - 1) * nruns + kc;
+        int c = 0;
+        for (int seg = 0; seg < nseg && ok; ++seg) {
+          const bool hh = seg == nbase - 1;
+          for (int q0 = 0; q0 < kc; ++c, ++gc) {
+            q0 = hh ? q0 + 1 : sparse_run_end(kl, kc, gsz, q0);
+            const int b = (int)(gc & 1);
+            bool w = mbar_wait<PAIR>(&tfull[b], (uint32_t)(gc >> 1) & 1u, abortf, p.wait_ns);
+            w = __all_sync(0xffffffffu, w);
+            if (!w) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            if (pf && c == nch - 2)
+              asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf),
+                           "r"((uint32_t)(TCOLS * sizeof(float)))
+                           : "memory");
+            float wgt = 1.0f;
+            if constexpr (F16) wgt = hh ? 1.0f : 1.0f / kLoScale;
+#pragma unroll
+            for (int c0 = 0; c0 < TCOLS; c0 += 16) {
+              uint32_t v[16];
+              tmem_ld16(trow + (uint32_t)b * ACC_COLS + (uint32_t)c0, v);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) acc[c0 + j] = fmaf(wgt, __uint_as_float(v[j]), acc[c0 + j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              if (!issuer)
+                mbar_arrive_cluster(tempty_peer + (uint32_t)(b * sizeof(uint64_t)));
+              else
+                mbar_arrive(&tempty[b]);
+            }
+          }
+        }
+        if (!ok || *((volatile int*)abortf)) break;
+        tile_end<KIND, EPI>(p, acc, tix, tix * CG + (int)rank, it, e, lane, grp, r, sg, red);
+        continue;
+      }
       int kb0 = 0;
       for (int c = 0; c < nchunks; ++c, ++gc) {
         const int b = (int)(gc & 1);
@@ -881,10 +1046,10 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int bo
 // one launch of the (KIND, EPI, CG) kernel over `units` CTAs or CTA pairs (at most
 // the resident ones), with its shared-memory attribute and its resident-pair
 // count queried once
-template <int KIND, int EPI, int CG>
+template <int KIND, int EPI, int CG, bool SPARSE = false>
 cudaError_t launch_kind(const KMaps& maps, const KParams& p, int units, cudaStream_t s) {
   static int resident = 0;
-  auto kern = k_gemm_tc<KIND, EPI, CG>;
+  auto kern = k_gemm_tc<KIND, EPI, CG, SPARSE>;
   constexpr int smem = Ring<CG>::SMEM_BYTES;
   if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -939,6 +1104,14 @@ cudaError_t launch_epi(int epi, const KMaps& maps, const KParams& p, int units, 
   if (epi == EPI_SQUARE) return launch_kind<KIND, EPI_SQUARE, CG>(maps, p, units, s);
   if (epi == EPI_SYMM) return launch_kind<KIND, EPI_SYMM, CG>(maps, p, units, s);
   return launch_kind<KIND, EPI_PLAIN, CG>(maps, p, units, s);
+}
+
+// the block-sparse square: one launch over every resident pair, the tile count
+// read on the device
+cudaError_t launch_sparse(int kind, const KMaps& maps, const KParams& p, int units, cudaStream_t s) {
+  if (kind == KIND_FP16X2) return launch_kind<KIND_FP16X2, EPI_SQUARE, 2, true>(maps, p, units, s);
+  if (kind == KIND_BF16X3) return launch_kind<KIND_BF16X3, EPI_SQUARE, 2, true>(maps, p, units, s);
+  return launch_kind<KIND_BF16X2, EPI_SQUARE, 2, true>(maps, p, units, s);
 }
 
 template <int CG>
@@ -1041,6 +1214,17 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   p.withhold = L.tune.withhold;
   p.tail = L.tail;
   // persistent: one CTA per SM (the shared-memory ring allows no second one)
+  p.dyn_ntiles = L.dyn_ntiles;
+  p.kcnt = L.kcnt;
+  p.klist = L.klist;
+  p.nbk = L.nbk;
+  if (L.dyn_ntiles) {
+    if (cg != 2 || L.epi != EPI_SQUARE || L.tail || !L.kcnt || !L.klist || L.nbk * 256 != np) {
+      snprintf(errbuf, errlen, "tcgen05 product: block-sparse launches are squares on CTA pairs");
+      return cudaErrorInvalidValue;
+    }
+    return launch_sparse(kind, maps, p, L.ntiles, s);
+  }
   // persistent: one CTA (pair) per SM (pair of SMs), the launch's tiles spread over them
   if (cg == 2) return launch_cg<2>(kind, L.epi, maps, p, L.ntiles, s);
   return launch_cg<1>(kind, L.epi, maps, p, L.ntiles, s);

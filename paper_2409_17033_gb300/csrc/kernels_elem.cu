@@ -269,6 +269,11 @@ __global__ void k_decide(const Part3* part, DevState* st, DecideParams p) {
       if (s >= 3 && st->sigma[s - 2] != st->sigma[s - 1] && st->f[s - 2] <= p.floor_gate &&
           st->f[s] >= st->f[s - 2])
         floor_stop = true;
+      // block-sparse recursion: from f <= 1e-4 a pair of opposite steps cuts f at
+      // least 600-fold in exact arithmetic; less than twofold is the threshold's floor
+      if (!floor_stop && p.ratio_floor && s >= 3 && st->sigma[s - 2] != st->sigma[s - 1] &&
+          st->f[s - 2] <= kRatioGate && st->f[s] >= 0.5 * st->f[s - 2])
+        floor_stop = true;
       if (!floor_stop && s > kStall) {
         double best = st->f[1];
         for (int k = 2; k <= s - kStall; ++k) best = fmin(best, st->f[k]);

@@ -390,6 +390,72 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   return SP2_OK;
 }
 
+// Workspace of the block-sparse recursion at padded size np.
+int sparse_bufs(sp2_handle_t h, int64_t np, double tau, SparseBufs* B) {
+  const int nb = (int)(np / 256);
+  const size_t nt = (size_t)nb * (nb + 1) / 2;
+  B->nb = nb;
+  B->tau2 = tau * tau;
+  void* p;
+  for (int i = 0; i < 2; ++i) {
+    const std::string k = std::to_string(i);
+    TRY(ws(h, "sp.mask" + k, (size_t)nb * nb, &p));
+    B->mask[i] = static_cast<uint8_t*>(p);
+    TRY(ws(h, "sp.tiles" + k, nt * sizeof(Tile), &p));
+    B->tiles[i] = static_cast<Tile*>(p);
+    TRY(ws(h, "sp.ntiles" + k, sizeof(int), &p));
+    B->ntiles[i] = static_cast<int*>(p);
+    TRY(ws(h, "sp.kcnt" + k, nt * sizeof(int), &p));
+    B->kcnt[i] = static_cast<int*>(p);
+    TRY(ws(h, "sp.klist" + k, nt * nb * sizeof(uint16_t), &p));
+    B->klist[i] = static_cast<uint16_t*>(p);
+  }
+  TRY(ws(h, "sp.zero", nt * sizeof(uint32_t), &p));
+  B->zero = static_cast<uint32_t*>(p);
+  TRY(ws(h, "sp.nzero", sizeof(int), &p));
+  B->nzero = static_cast<int*>(p);
+  TRY(ws(h, "sp.nrm2", (size_t)nb * nb * sizeof(double), &p));
+  B->nrm2 = static_cast<double*>(p);
+  TRY(ws(h, "sp.psum", sizeof(Part3), &p));
+  B->psum = static_cast<Part3*>(p);
+  return SP2_OK;
+}
+
+// The block-sparse square of `step` over the tiles and K lists the plan wrote
+// into tiles[step % 2] (their count on the device); two partials per tile.
+int sparse_square(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, const SparseBufs& B) {
+  sp2_handle_t h = c.h;
+  const int tl = step % 2;
+  TcLaunch L;
+  TRY(tc_common(c, &L, B.nb * (B.nb + 1) / 2));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.timing) {
+    TRY(ev_pair(c, &e0, &e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  char eb[256] = {0};
+  L.epi = EPI_SQUARE;
+  L.P = TcOperand{xin.hi, xin.lo, c.np, xin.mid};
+  L.Q = L.P;
+  L.out = xout;
+  L.prev = static_cast<const float*>(xin.master);
+  L.tiles = B.tiles[tl];
+  L.step = step;
+  L.dyn_ntiles = B.ntiles[tl];
+  L.kcnt = B.kcnt[tl];
+  L.klist = B.klist[tl];
+  L.nbk = B.nb;
+  cudaError_t e = launch_gemm_tc(L, h->stream, eb, sizeof eb);
+  if (e != cudaSuccess) return fail(h, SP2_ECUDA, "block-sparse square: %s %s", cudaGetErrorString(e), eb);
+  if (c.timing) {
+    CK(cudaEventRecord(e1, h->stream));
+    c.timed.push_back({step, 0});
+  }
+  c.launches++;
+  c.kernels++;
+  return SP2_OK;
+}
+
 // Y_{n+1} = (1 - sigma_n) Y_n + sigma_n (Y_n X_n + X_n Y_n) for a batch of Y.
 // Default: Z = Y X (tcgen05 EPI_PLAIN in split modes, CUDA cores otherwise), then
 // the transpose-add kernel. With the handle's fused_response option (split modes):
@@ -552,6 +618,8 @@ int validate_opts(sp2_handle_t h, const sp2_opts* o) {
   if (o->ckpt_k < 1 && o->ckpt_k != SP2_CKPT_AUTO)
     return fail(h, SP2_EINVAL, "ckpt_k must be >= 1 or SP2_CKPT_AUTO");
   if (!(o->tail_f >= 0.0)) return fail(h, SP2_EINVAL, "tail_f must be >= 0");
+  if (o->block_sparse && !(o->block_tau >= 0.0 && !std::isinf(o->block_tau)))
+    return fail(h, SP2_EINVAL, "block_tau must be finite and >= 0");
   return SP2_OK;
 }
 
@@ -611,6 +679,7 @@ struct Sp2Out {
   MatBuf xout;    // X_{M+1} (the kept floor candidate when the stop backtracked: master only)
   MatBuf yout;    // Y_{M+1}, likewise
   int stop_step = 0;  // the step after which the stop test fired (>= M)
+  bool sparse = false;   // block-sparse recursion (info reports the formed block share)
 };
 
 // Runs Eq. DM0 on the padded X_1 = alpha I + beta H. If ybatch > 0, the
@@ -627,6 +696,16 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
             Ctx& c, Sp2Out* out) {
   const int64_t np = pad_n(n);
   const int mode = o.mode;
+  const bool sparse = o.block_sparse != 0;
+  if (sparse) {
+    if (!split_mode(mode) || !h->tune.pair)
+      return fail(h, SP2_EINVAL, "block_sparse: the squares run in the split modes on CTA pairs");
+    if (ybatch > 0 || keep)
+      return fail(h, SP2_EINVAL, "block_sparse: sp2_density without keep_history only");
+    if (o.tail_f > 0.0) return fail(h, SP2_EINVAL, "block_sparse with tail_f > 0");
+    if (np / 256 > kMaxSparseBlocks)
+      return fail(h, SP2_EINVAL, "block_sparse: N above %d", 256 * kMaxSparseBlocks);
+  }
   CK(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), h->stream));
   // spectral bounds (Sec. II) and X_1 = alpha I + beta H, on the device
   if (o.eps_min < o.eps_max) {
@@ -661,7 +740,22 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   c.tail = dp.tail_f > 0.0 ? 1 : 0;
   dp.n = 1;
   dp.nparts = ni;
-  CK(launch_decide(c.part, c.st, dp, h->stream));
+  SparseBufs sb;
+  if (sparse) {
+    // X~_1 = T_tau(X_1); the first square's tiles; X[0]'s content is unknown, so
+    // every block of it counts as stale for the first square
+    TRY(sparse_bufs(h, np, o.block_tau, &sb));
+    CK(launch_block_norms(static_cast<const float*>(X[1].master), np, sb.nb, sb.nrm2, h->stream));
+    CK(cudaMemsetAsync(sb.mask[0], 1, (size_t)sb.nb * sb.nb, h->stream));
+    CK(launch_sparse_plan(sb, 1, 1, 0, 1, c.part, ni, c.st, 0, h->stream));
+    CK(launch_zero_blocks(sb, X[1], np, mode, c.st, 0, 1, h->stream));
+    c.kernels += 3;
+    dp.nparts = 1;
+    dp.ratio_floor = 1;
+    CK(launch_decide(sb.psum, c.st, dp, h->stream));
+  } else {
+    CK(launch_decide(c.part, c.st, dp, h->stream));
+  }
   c.kernels++;
   ScaleBuf sc;
   if (ybatch > 0) {
@@ -716,11 +810,20 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
     if (ybatch > 0)
       TRY(response_step(c, xin, Y[step % 2], Y[(step + 1) % 2], ybatch, step, sc, step % 2,
                         (step + 1) % 2));
-    int nparts = 0;
-    TRY(square_step(c, xin, xo, step, &nparts));
     dp.n = step + 1;
-    dp.nparts = nparts;
-    CK(launch_decide(c.part, c.st, dp, h->stream));
+    if (sparse) {
+      TRY(sparse_square(c, xin, xo, step, sb));
+      CK(launch_sparse_plan(sb, 0, (step + 1) % 2, step % 2, (step + 1) % 2, c.part, 0, c.st, step,
+                            h->stream));
+      CK(launch_zero_blocks(sb, xo, np, mode, c.st, step, 0, h->stream));
+      c.kernels += 2;
+      CK(launch_decide(sb.psum, c.st, dp, h->stream));
+    } else {
+      int nparts = 0;
+      TRY(square_step(c, xin, xo, step, &nparts));
+      dp.nparts = nparts;
+      CK(launch_decide(c.part, c.st, dp, h->stream));
+    }
     c.kernels++;
     if (track) {
       CK(launch_keep_best(xin.master, xbest.master, np * np, mode, c.st, step, h->stream));
@@ -767,6 +870,13 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
   c.flops = f0 + fstep * out->stop_step;
   c.alg = a0 + astep * out->stop_step;
   c.launches = l0 + lstep * out->stop_step;
+  if (sparse) {
+    // per listed K block of a 256 x 256 tile: 256^3 products of every split term
+    const double w = S.work_kblocks * 2.0 * 256.0 * 256.0 * 256.0 * k_mult(mode);
+    c.flops = f0 + w;
+    c.alg = a0 + w;
+    out->sparse = true;
+  }
   return SP2_OK;
 }
 
@@ -786,6 +896,12 @@ void fill_info(sp2_handle_t h, const Sp2Out& r, const Ctx& c, sp2_info* info) {
   info->trace = s.t1[r.M + 1];
   info->idem_err = s.t1[r.M + 1] - s.t2[r.M + 1];
   for (int i = 1; i <= r.M; ++i) info->tail_single_steps += s.plane1[i] ? 1 : 0;
+  if (r.sparse && r.M > 0) {
+    // mean over the steps of the result (1..M) of the upper blocks each square formed
+    double fs = 0.0;
+    for (int i = 1; i <= r.M; ++i) fs += s.fill[i];
+    info->block_fill = fs / r.M;
+  }
   info->n_gemm_launches = c.launches;
   info->executed_flops = c.flops;
   info->algorithmic_flops = c.alg;
@@ -1635,6 +1751,7 @@ int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, do
   if (N > 0 && (!H || (K > 0 && (!B || !D1)))) return fail(h, SP2_EINVAL, "null pointer");
   sp2_opts o = resolve(opts_in);
   TRY(validate_opts(h, &o));
+  if (o.block_sparse) return fail(h, SP2_EINVAL, "block_sparse: sp2_density only");
   if (info) memset(info, 0, sizeof *info);
   if (N == 0) {
     if (info) info->converged = 1;
@@ -1743,6 +1860,7 @@ int sp2_nonorth_susceptibility(sp2_handle_t h, const void* H, const void* S, int
   if (N > 0 && (!S || !A || !D || !WH || !WS)) return fail(h, SP2_EINVAL, "null pointer");
   sp2_opts o = resolve(opts_in);
   TRY(validate_opts(h, &o));
+  if (o.block_sparse) return fail(h, SP2_EINVAL, "block_sparse: sp2_density only");
   if (o.fixed_m > 0) return fail(h, SP2_EINVAL, "fixed_m is not supported here");
   if (info) memset(info, 0, sizeof *info);
   if (N == 0) {
@@ -2098,6 +2216,7 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
     return fail(h, SP2_EINVAL, "finite-T SCF: mu must be finite, n_doublings <= 64");
   sp2_opts o = resolve(opts_in);
   TRY(validate_opts(h, &o));
+  if (o.block_sparse) return fail(h, SP2_EINVAL, "block_sparse: sp2_density only");
   const bool refine = so->refine_below > 0.0 && so->refine_mode != o.mode;
   if (refine && so->refine_mode != SP2_MODE_FP64 && so->refine_mode != SP2_MODE_FP32 &&
       so->refine_mode != SP2_MODE_BF16X2 && so->refine_mode != SP2_MODE_FP16X2 &&

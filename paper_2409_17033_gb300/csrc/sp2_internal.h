@@ -28,6 +28,7 @@ struct DevState {
   double f[SP2_MAX_ITER + 2];    // ||X_n - X_n^2||_F^2, known after step n
   int sigma[SP2_MAX_ITER + 2];   // sigma_n, the branch taken by step n (X_n -> X_{n+1})
   int plane1[SP2_MAX_ITER + 2];  // split-tail mode: 1 if step n uses the hi planes alone
+  double fill[SP2_MAX_ITER + 2]; // block-sparse: share of the upper blocks step n formed
   int stop_at;                   // M once a stop rule fired, else 0
   int nonfinite;                 // a trace was NaN/Inf
   int abort_flag;                // a device wait timed out (kernel bailed out)
@@ -39,6 +40,7 @@ struct DevState {
   int backtracked;               // the floor stop returned X_nbest, not the last iterate
   int stop_step;                 // the step after which the stop test fired
   double alpha, beta;            // X_1 = alpha I + beta H, from the (widened) bounds
+  double work_kblocks;           // block-sparse: 256-wide K blocks the squares ran, all tiles
 };
 // The host reads the trailing part of DevState (from stop_at on) after every step.
 inline size_t devstate_tail_offset() { return offsetof(DevState, stop_at); }
@@ -163,7 +165,9 @@ struct DecideParams {
   int min_iter, max_iter;
   int fixed_m;       // > 0: sigma preset, stop when n - 1 == fixed_m
   double tail_f;     // > 0: single-plane products while f of the last iterate exceeds it
+  int ratio_floor = 0;  // block-sparse recursion: the threshold-floor test as well
 };
+constexpr double kRatioGate = 1e-4;   // f from which a pair of opposite steps must cut f 600-fold
 cudaError_t launch_decide(const Part3* part, DevState* st, DecideParams p, cudaStream_t s);
 // copy `count` entries of the master src -> dst when st->keep_step == step (the
 // floor candidate with the smallest f so far), else nothing
@@ -240,8 +244,43 @@ struct TcLaunch {
   float* zmax = nullptr;           // FP16X2 EPI_PLAIN: per batch entry, receives max |C|
   int tail = 0;                    // split-tail mode (st->plane1 decides per step)
   TcTuning tune;
+  // block-sparse square (CTA pairs): tiles, their count and their K-block lists
+  // are written on the device by the plan kernel; ntiles is then the upper bound
+  const int* dyn_ntiles = nullptr;
+  const int* kcnt = nullptr;
+  const uint16_t* klist = nullptr;
+  int nbk = 0;                     // K blocks of 256 (np / 256): the stride of klist
 };
 cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size_t errlen);
+
+// ---- block-sparse recursion (sparse_kernels.cu): 256 x 256 blocks, N <= 65536
+constexpr int kMaxSparseBlocks = 256;
+struct SparseBufs {
+  int nb = 0;                      // blocks per dimension (np / 256)
+  double tau2 = 0.0;               // a block stays when its norm^2 > tau2 (or it is diagonal)
+  uint8_t* mask[2] = {};           // content mask of X[0], X[1] (nb x nb, symmetric)
+  Tile* tiles[2] = {};             // tile lists, by step parity (step n squares tiles[n % 2])
+  int* ntiles[2] = {};
+  int* kcnt[2] = {};
+  uint16_t* klist[2] = {};         // nb K blocks per tile
+  uint32_t* zero = nullptr;        // blocks to zero: (I << 16) | J, I <= J
+  int* nzero = nullptr;
+  double* nrm2 = nullptr;          // nb x nb scratch: block norms^2
+  Part3* psum = nullptr;           // the decision's one partial: traces of X~, and f
+};
+// ||block||_F^2 of the upper blocks of a master into nrm2
+cudaError_t launch_block_norms(const float* master, int64_t np, int nb, double* nrm2,
+                               cudaStream_t s);
+// threshold the iterate just formed (init: X_1 from nrm2 and the init partials;
+// else the square of `step`, from its two partials per tile), list the blocks to
+// zero in buffer xo, reduce the decision's partial, and write the next square's
+// tiles and K lists into tiles[tl_out]. No-op after the stop (but for init).
+cudaError_t launch_sparse_plan(const SparseBufs& B, int init, int xo, int tl_in, int tl_out,
+                               const Part3* part, int nparts_init, DevState* st, int step,
+                               cudaStream_t s);
+// zero the listed blocks (and mirrors) of x's master and planes
+cudaError_t launch_zero_blocks(const SparseBufs& B, MatBuf x, int64_t np, int mode,
+                               const DevState* st, int step, int init, cudaStream_t s);
 void tc_tile_shape(int pair, int* bm, int* bn);   // output tile of one CTA (pair)
 
 // FP16X2 scale of the next symmetric response step: per batch entry, the sum of
