@@ -474,6 +474,111 @@ __device__ __forceinline__ uint2 pack4(const uint16_t (&v)[4]) {
   return make_uint2(v[0] | ((uint32_t)v[1] << 16), v[2] | ((uint32_t)v[3] << 16));
 }
 
+// ---- vectorised forms of the O(N^2) passes for an FP32 input with N % 4 == 0:
+// four consecutive entries per thread step, FP64 only where the values need it
+// (GB300 runs FP64 at a small fraction of its FP32 rate)
+
+// planes of four stored entries in the mode's split (fp16 planes with scale 1)
+__device__ __forceinline__ void store_planes4(MatBuf d, int mode, int64_t t, const float (&f)[4]) {
+  uint16_t h[4], l[4], md[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (mode == SP2_MODE_BF16X3) split_bf16x3(f[k], h[k], md[k], l[k]);
+    else if (mode == SP2_MODE_BF16X2) split_bf16(f[k], h[k], l[k]);
+    else split_fp16(f[k], 1.0f, h[k], l[k]);
+  }
+  reinterpret_cast<uint2*>(d.hi)[t] = pack4(h);
+  reinterpret_cast<uint2*>(d.lo)[t] = pack4(l);
+  if (mode == SP2_MODE_BF16X3) reinterpret_cast<uint2*>(d.mid)[t] = pack4(md);
+}
+
+// X_1 = alpha I + beta H (coefficients from st) with its planes: the same stored
+// values as k_init (beta h + alpha in FP64, rounded once); the trace partials
+// add the squares of four stored entries in FP32 before FP64
+__global__ void k_init_x4(const float* __restrict__ src, int64_t n, int64_t np, int mode,
+                          MatBuf dst, Part3* part, const DevState* st) {
+  const double alpha = st->alpha, beta = st->beta;
+  double t1 = 0.0, t2 = 0.0;
+  const int64_t q = np / 4;
+  for (int64_t r = blockIdx.x; r < np; r += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < q; c += blockDim.x) {
+      const int64_t j = 4 * c;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (r < n && j < n) {   // n % 4 == 0: the whole group is inside
+        const float4 h = *reinterpret_cast<const float4*>(src + r * n + j);
+        x[0] = h.x;
+        x[1] = h.y;
+        x[2] = h.z;
+        x[3] = h.w;
+      }
+      float f[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double v = (r < n && j + k < n) ? beta * (double)x[k] : 0.0;
+        if (r < n && j + k == r) v += alpha;
+        f[k] = (float)v;
+      }
+      reinterpret_cast<float4*>(dst.master)[r * q + c] = make_float4(f[0], f[1], f[2], f[3]);
+      store_planes4(dst, mode, r * q + c, f);
+      t2 += (double)(f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3]);
+      if (r >= j && r < j + 4) t1 += (double)f[r - j];
+    }
+  }
+  t1 = block_sum(t1);
+  __syncthreads();
+  t2 = block_sum(t2);
+  if (threadIdx.x == 0) part[blockIdx.x] = Part3{t1, t2, 0.0};
+}
+
+// Gershgorin discs of an FP32 H, one warp per row (FP64 row sums)
+__global__ void k_bounds_x4(const float* __restrict__ H, int64_t n, double2* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
+    const float* row = H + i * n;
+    double r = 0.0, d = 0.0;
+    for (int64_t c = lane; c < n / 4; c += 32) {
+      const float4 h = *reinterpret_cast<const float4*>(row + 4 * c);
+      const float x[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (4 * c + k == i) d = x[k];
+        else r += fabs((double)x[k]);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      r += __shfl_xor_sync(0xffffffffu, r, o);
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if (lane == 0) {
+      lo = nmin(lo, d - r);
+      hi = nmax(hi, d + r);
+    }
+  }
+  double2 mm = block_minmax(lo, hi);
+  if (threadIdx.x == 0) part[blockIdx.x] = mm;
+}
+
+// caller-layout copy of an FP32 master, four entries per step; the same values
+// as k_copy_out (FP64 product with the scale, rounded once) when scaled
+__global__ void k_copy_out_x4(const float* __restrict__ src, int64_t n, int64_t np, int64_t batch,
+                              double scale, float* __restrict__ dst, const DevState* beta_state) {
+  if (beta_state) scale *= beta_state->beta;
+  const int64_t q = n / 4, per = n * q, total = batch * per;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / per, rem = t % per, i = rem / q, c = rem % q;
+    float4 v = *reinterpret_cast<const float4*>(src + (b * np + i) * np + 4 * c);
+    if (scale != 1.0) {
+      v.x = (float)((double)v.x * scale);
+      v.y = (float)((double)v.y * scale);
+      v.z = (float)((double)v.z * scale);
+      v.w = (float)((double)v.w * scale);
+    }
+    reinterpret_cast<float4*>(dst)[t] = v;
+  }
+}
+
 // hi/lo (and BF16X3 mid) planes from the FP32 master; total is a multiple of 4
 __global__ void k_split(MatBuf m, int64_t total, int mode) {
   const int64_t total4 = total / 4;
@@ -671,7 +776,10 @@ int bounds_nparts(int64_t n) { return (int)(n < 1024 ? (n < 1 ? 1 : n) : 1024); 
 
 cudaError_t launch_bounds(const void* H, int64_t n, int dtype, double2* part, int nparts,
                           DevState* st, cudaStream_t s) {
-  k_bounds<<<nparts, kRedThreads, 0, s>>>(H, n, dtype, part);
+  if (dtype == SP2_F32 && n % 4 == 0 && (reinterpret_cast<uintptr_t>(H) & 15u) == 0)
+    k_bounds_x4<<<nparts, kRedThreads, 0, s>>>(static_cast<const float*>(H), n, part);
+  else
+    k_bounds<<<nparts, kRedThreads, 0, s>>>(H, n, dtype, part);
   k_bounds_final<<<1, 1024, 0, s>>>(part, nparts, st);
   return cudaGetLastError();
 }
@@ -682,6 +790,12 @@ cudaError_t launch_init(const void* src, int64_t n, int64_t np, int64_t batch, i
                         int diag_only, int symmetrize, double alpha, double beta, int mode,
                         MatBuf dst, Part3* part, int nparts, float* ymax, cudaStream_t s,
                         int coef, const DevState* st) {
+  if (coef == INIT_STATE && part && batch == 1 && dtype == SP2_F32 && !diag_only && !symmetrize &&
+      !ymax && split_mode(mode) && n % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    k_init_x4<<<nparts, kRedThreads, 0, s>>>(static_cast<const float*>(src), n, np, mode, dst, part,
+                                             st);
+    return cudaGetLastError();
+  }
   int grid = part ? nparts : grid_for(batch * np, 1, 4096);
   k_init<<<grid, kRedThreads, 0, s>>>(src, n, np, batch, dtype, diag_only, symmetrize, alpha,
                                       beta, mode, dst, part, ymax, coef, st);
@@ -750,6 +864,13 @@ cudaError_t launch_symm_update(const void* Z, MatBuf y_in, MatBuf y_out, int64_t
 cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, int mode,
                             double scale, void* dst, int dtype, cudaStream_t s,
                             const DevState* beta_state) {
+  if (mode != SP2_MODE_FP64 && dtype == SP2_F32 && n % 4 == 0 &&
+      (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+    k_copy_out_x4<<<grid_for(batch * n * n / 4, 256, 8192), 256, 0, s>>>(
+        static_cast<const float*>(src.master), n, np, batch, scale, static_cast<float*>(dst),
+        beta_state);
+    return cudaGetLastError();
+  }
   k_copy_out<<<grid_for(batch * n * n, 256, 8192), 256, 0, s>>>(src, n, np, batch, mode, scale,
                                                                  dst, dtype, beta_state);
   return cudaGetLastError();

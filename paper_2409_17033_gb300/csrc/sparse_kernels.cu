@@ -43,7 +43,7 @@ __global__ void k_block_norms(const float* __restrict__ x, int64_t np, int nb, d
     const int r = t / (kBlk / 4), c4 = t % (kBlk / 4);
     const float4 v = *reinterpret_cast<const float4*>(x + ((int64_t)I * kBlk + r) * np +
                                                       (int64_t)J * kBlk + 4 * c4);
-    acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    acc += (double)(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);   // four in FP32, then FP64
   }
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
