@@ -154,8 +154,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Wait for the phase of parity `parity` to complete. Gives up (returning
 // false) when the abort flag is raised or after limit_ns, raising the flag.
 template <bool CL = false>
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag,
-                          unsigned long long limit_ns) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* abort_flag,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait<CL>(bar, parity)) return true;   // no clock read when it is ready
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait<CL>(bar, parity)) return true;
@@ -226,6 +227,23 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+
+// Stage and phase parity of a running k-block counter in a ring of STAGES
+// stages, advanced by one per k-block without a division: the loops of the
+// copy issuer and the MMA issuer (one thread each) are on the tensor pipe's
+// critical path, and a 64-bit division by the stage count per k-block
+// measurably delayed the MMA issue.
+template <int STAGES>
+struct RingPos {
+  int s = 0;
+  uint32_t ph = 0;
+  __device__ __forceinline__ void next() {
+    if (++s == STAGES) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
 
 // Shared-memory matrix descriptor for a K-major tile written by TMA with
 // 128-byte swizzling: rows of 128 B, 8-row atoms of 1024 B (SBO = 1024),
@@ -685,6 +703,7 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
      if (lane == 0) {
       // block-sparse square: every segment walks the tile's listed K blocks
       int64_t g = 0;
+      RingPos<STAGES> rp;
       bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it) {
         const int tix = unit + it * nunits;
@@ -694,9 +713,9 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
         for (int seg = 0; seg < nseg && ok; ++seg) {
           int pa, pb;
           seg_planes<KIND>(seg, nbase, pa, pb);
-          for (int u = 0; u < 4 * kc; ++u, ++g) {
-            const int s = (int)(g % STAGES);
-            const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          for (int u = 0; u < 4 * kc; ++u, ++g, rp.next()) {
+            const int s = rp.s;
+            const uint32_t ph = rp.ph;
             if (!mbar_wait<PAIR>(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
               ok = false;
               break;
@@ -723,20 +742,25 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
       const int nkb = p.nkb;
       // k-block counter g runs on across tiles: stage g % STAGES, phase (g / STAGES) & 1
       int64_t g = 0;
+      RingPos<STAGES> rp;
       bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it) {
         const Tile t = p.tiles[unit + it * nunits];
         const int bat = (int)(t.row0 / np);
-        for (int kb = 0; kb < total_kb; ++kb, ++g) {
-          const int s = (int)(g % STAGES);
-          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+        int seg = 0, kin = -1;   // segment of k-block kb and its k-block within the segment
+        for (int kb = 0; kb < total_kb; ++kb, ++g, rp.next()) {
+          if (++kin == nkb) {
+            kin = 0;
+            ++seg;
+          }
+          const int s = rp.s;
+          const uint32_t ph = rp.ph;
           if (!mbar_wait<PAIR>(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
             ok = false;
             break;
           }
           if (p.withhold && blockIdx.x == 0 && g == 0) continue;  // test hook: never completes
-          const int seg = kb / nkb;
-          const int kx = (kb - seg * nkb) * BK;
+          const int kx = kin * BK;
           const bool swap = EPI == EPI_SYMM && seg >= nbase;   // second half: [Q | .] . [. ; P]
           int pa, pb;
           seg_planes<KIND>(swap ? seg - nbase : seg, nbase, pa, pb);
@@ -770,15 +794,17 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
         total = 0;
         for (int it = 0; it < my_tiles; ++it) total += (int64_t)nseg * 4 * p.kcnt[unit + it * nunits];
       }
-      for (int64_t g = 0; g < total; ++g) {
-        const int s = (int)(g % STAGES);
-        if (!mbar_wait<PAIR>(&full[s], (uint32_t)(g / STAGES) & 1u, abortf, p.wait_ns)) break;
-        mbar_arrive_cluster_release(pfull_peer + (uint32_t)(s * sizeof(uint64_t)));
+      RingPos<STAGES> rp;
+      for (int64_t g = 0; g < total; ++g, rp.next()) {
+        if (!mbar_wait<PAIR>(&full[rp.s], rp.ph, abortf, p.wait_ns)) break;
+        mbar_arrive_cluster_release(pfull_peer + (uint32_t)(rp.s * sizeof(uint64_t)));
       }
     } else if constexpr (SPARSE) {
      if (lane == 0 && issuer) {
       bool ok = true;
       int64_t g = 0, gc = 0;
+      RingPos<STAGES> rp;
+      const uint64_t adesc0 = sdesc_sw128(smem_u32(smem));
       for (int it = 0; it < my_tiles && ok; ++it) {
         const int tix = unit + it * nunits;
         const int kc = p.kcnt[tix];
@@ -794,18 +820,17 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
             }
             tc_fence_after();
             const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
-            for (int u = 4 * q0; u < 4 * q1; ++u, ++g) {
-              const int s = (int)(g % STAGES);
-              const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-              if (!mbar_wait<PAIR>(&full[s], ph, abortf, p.wait_ns) ||
+            for (int u = 4 * q0; u < 4 * q1; ++u, ++g, rp.next()) {
+              const int s = rp.s;
+              const uint32_t ph = rp.ph;
+              if (!mbar_wait<false>(&full[s], ph, abortf, p.wait_ns) ||
                   !mbar_wait<PAIR>(&pfull[s], ph, abortf, p.wait_ns)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
-              const uint64_t adesc = sdesc_sw128(a_addr);
-              const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
+              const uint64_t adesc = adesc0 + (uint64_t)(s * (STAGE_BYTES >> 4));
+              const uint64_t bdesc = adesc + (uint64_t)(A_BYTES >> 4);
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k)
                 umma_f16<CG>(dtm, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), kIdesc,
@@ -825,10 +850,21 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
     } else if (lane == 0 && issuer) {
       bool ok = true;
       int64_t g = 0, gc = 0;   // k-block and chunk counters across tiles
+      RingPos<STAGES> rp;
+      // descriptors of a stage: the ring's base descriptor plus the stage offset in
+      // 16-byte units (the address field holds bits 4-17 of a shared-memory address
+      // below 256 KB, so the addition never carries out of it)
+      const uint64_t adesc0 = sdesc_sw128(smem_u32(smem));
       for (int it = 0; it < my_tiles && ok; ++it) {
         int kb0 = 0;   // first k-block of chunk c within the tile
+        int segb = 0, kin = 0;   // base segment (seg % nbase) and k-block within the segment
         for (int c = 0; c < nchunks && ok; ++c, ++gc) {
-          const int len = chunk_len(kb0);
+          const int len = segb == nbase - 1 ? ch_hi : ch_lo;   // chunk_len(kb0), no division
+          kin += len;
+          if (kin == p.nkb) {
+            kin = 0;
+            if (++segb == nbase) segb = 0;
+          }
           const int b = (int)(gc & 1);
           // the epilogue (of both CTAs of a pair) has drained buffer b (chunk gc-2)
           if (!mbar_wait<PAIR>(&tempty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abortf, p.wait_ns)) {
@@ -837,18 +873,19 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
           }
           tc_fence_after();
           const uint32_t dtm = tmem + (uint32_t)b * ACC_COLS;
-          for (int kb = kb0; kb < kb0 + len; ++kb, ++g) {
-            const int s = (int)(g % STAGES);
-            const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-            if (!mbar_wait<PAIR>(&full[s], ph, abortf, p.wait_ns) ||
+          for (int kb = kb0; kb < kb0 + len; ++kb, ++g, rp.next()) {
+            const int s = rp.s;
+            const uint32_t ph = rp.ph;
+            // this CTA's own stage (its own copies: CTA-scope acquire), then, on a
+            // pair, the peer's stage as relayed by its warp 1
+            if (!mbar_wait<false>(&full[s], ph, abortf, p.wait_ns) ||
                 (PAIR && !mbar_wait<PAIR>(&pfull[s], ph, abortf, p.wait_ns))) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
-            const uint64_t adesc = sdesc_sw128(a_addr);
-            const uint64_t bdesc = sdesc_sw128(a_addr + A_BYTES);
+            const uint64_t adesc = adesc0 + (uint64_t)(s * (STAGE_BYTES >> 4));
+            const uint64_t bdesc = adesc + (uint64_t)(A_BYTES >> 4);
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
               // advance 16 elements = 32 bytes along K inside the swizzled row: +2 in 16-byte units
@@ -1187,11 +1224,15 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
   // exact form, 512-wide 2.5e-5 and 2048-wide 7.6e-4, for 3% more time per
   // product than 512-wide chunks.
   p.ch = 4;
-  // The cross terms (hi*lo, lo*hi; in BF16X3 everything after hi*hi) are at most
-  // 2^-8 of the leading term once weighted, so the truncation bias of a longer
-  // TMEM accumulation shrinks with them: up to 2048-wide chunks (32 k-blocks,
-  // the largest power of two up to 32 that divides np / BK).
-  p.ch_lo = 32;
+  // The cross terms (hi*lo, lo*hi; in BF16X3 everything after hi*hi) are small
+  // once weighted, so the truncation bias of a longer TMEM accumulation shrinks
+  // with them: a chunk's bias scales with its length times the size of its
+  // terms. Every chunk boundary costs the MMA issuer a commit and a wait, so the
+  // cross terms take the longest chunk whose bias stays a few percent of the
+  // hi*hi chunks' (256 x 1): FP16X2 (weight 2^-11) up to 16384 wide (256
+  // k-blocks, 16384 x 2^-11 = 8), the bfloat16 modes (2^-8) up to 2048 (32
+  // k-blocks, also 8); the largest power of two up to that which divides np / BK.
+  p.ch_lo = f16 ? 256 : 32;
   while ((np / BK) % p.ch_lo != 0) p.ch_lo >>= 1;
   p.nbase = x3 ? 6 : 3;
   p.nseg = L.epi == EPI_SYMM ? 2 * p.nbase : p.nbase;
