@@ -34,9 +34,9 @@
 // accumulated in chunks, alternately in two TMEM buffers, and each chunk is
 // added into FP32 registers by the epilogue warps (the tensor core's own FP32
 // accumulation truncates, with a bias that grows with the chunk): 256-wide for
-// hi*hi, up to 2048-wide for the cross terms, whose weighted size is 2^-8 of it
-// or less. A tile starts with the long chunks, so the spare TMEM buffer covers
-// the previous tile's stores.
+// hi*hi, up to 16384-wide (FP16X2, weight 2^-11) or 2048-wide (bfloat16 modes,
+// 2^-8) for the cross terms. A tile starts with the long chunks, so the spare
+// TMEM buffer covers the previous tile's stores.
 //
 // CTA pairs (CG = 2, a cluster of two): a 256 x 256 tile per pair, one
 // tcgen05.mma.cta_group::2 stream of M = 256 issued by rank 0. Each CTA loads
@@ -596,7 +596,7 @@ __device__ __forceinline__ int sparse_run_end(const uint16_t* kl, int kc, int gs
 // SPARSE (square on CTA pairs only): the tile list, its length and every tile's
 // K blocks come from the device (the block-sparse plan); a tile's K axis is its
 // listed 256-wide blocks in each segment, hi*hi drained per block and a cross
-// term per run of listed blocks inside one dense 2048-wide chunk, so that with
+// term per run of listed blocks inside one dense cross-term chunk, so that with
 // every block listed the chunks, and the results, are the dense kernel's. The
 // sparse loops are separate from the dense ones, which the SPARSE = false
 // kernels alone contain.
