@@ -338,6 +338,27 @@ __device__ __forceinline__ void ld256f(const float* p, float* v) {
                : "memory");
 }
 
+// A sum of FP32 terms w x^2 (w a power of two) kept to about 2^-45 of its value
+// before it goes to FP64, at FP32 rates (GB300's FP64 rate is a small fraction
+// of its FP32 rate): each square enters as its rounded value plus its fmaf
+// residual (exact), each addition as TwoSum (Knuth) with its rounding error
+// carried in c. The _rn intrinsics keep the compiler from contracting the steps
+// into fused operations, which would lose the error terms.
+struct ExactSqSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add_sq(float w, float x) {
+    const float wx = w * x;                 // exact: w is 1 or 2
+    const float p = __fmul_rn(wx, x);
+    const float e = fmaf(wx, x, -p);        // wx x - p exactly
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // s + p - t
+    c = __fadd_rn(c, __fadd_rn(err, e));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // plane kinds of the product kernel
 constexpr int KIND_BF16X2 = 0, KIND_FP16X2 = 1, KIND_BF16X3 = 2;
 // plane indices of an operand: 0 = hi, 1 = lo, 2 = mid (BF16X3)
@@ -475,11 +496,13 @@ __device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], 
     // C for sigma > 0 and 2 M_n - C for sigma < 0 (M_n the previous iterate)
     const float os = (F16 && EPI == EPI_SYMM && p.o_scale) ? p.o_scale[bat] : 1.0f;
     const int64_t mbase = bat * np * np;   // first entry of this batch entry's matrix
-    // per-thread partials over at most 128 entries of one row in FP32 (GB300's FP64
-    // rate is a small fraction of its FP32 rate); lanes, warps and tiles add in FP64:
-    // Tr, ||.||_F^2 and (EPI_SQUARE) ||X_n - X_n^2||_F^2, whose residual is
-    // X_n - X_{n+1} up to its sign in either branch
-    float t1 = 0.0f, t2 = 0.0f, f = 0.0f;
+    // per-thread partials over at most 64 entries of one row, the squares summed
+    // with their rounding errors (FP64-equivalent); lanes, warps and tiles add in
+    // FP64: Tr, ||.||_F^2 and (EPI_SQUARE) ||X_n - X_n^2||_F^2, whose residual is
+    // X_n - X_{n+1} up to its sign in either branch. Tr takes the one diagonal
+    // entry a thread's row segment can hold, as it is.
+    float t1 = 0.0f;
+    ExactSqSum t2, f;
 #pragma unroll
     for (int c0 = 0; c0 < TCOLS; c0 += 16) {
       const int64_t gj0 = t.col0 + grp * TCOLS + c0;
@@ -504,8 +527,8 @@ __device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], 
           if (gj < li) continue;
           const float d = val[j], w2 = gj == li ? 1.0f : 2.0f;
           if (gj == li) t1 += d;
-          t2 = fmaf(w2 * d, d, t2);
-          if constexpr (EPI == EPI_SQUARE) f = fmaf(w2 * (xin[j] - d), xin[j] - d, f);
+          t2.add_sq(w2, d);
+          if constexpr (EPI == EPI_SQUARE) f.add_sq(w2, xin[j] - d);
         }
       }
       uint32_t wh[8], wl[8], wm[8];
@@ -557,7 +580,7 @@ __device__ __forceinline__ void tile_end(const KParams& p, float (&acc)[TCOLS], 
         if constexpr (X3) p.out_mid[o] = (uint16_t)(wm[j >> 1] >> sh);
       }
     }
-    double d1 = t1, d2 = t2, d3 = f;
+    double d1 = t1, d2 = t2.value(), d3 = f.value();
     for (int o = 16; o > 0; o >>= 1) {
       d1 += __shfl_xor_sync(0xffffffffu, d1, o);
       d2 += __shfl_xor_sync(0xffffffffu, d2, o);
