@@ -134,9 +134,19 @@ k_gemm_simt(const T* __restrict__ A, const T* __restrict__ X, int64_t np, int ep
 
 }  // namespace
 
-void simt_tile_shape(int mode, int* bm, int* bn) {
-  if (mode == SP2_MODE_FP64) { *bm = 64; *bn = 64; }
-  else { *bm = 128; *bn = 128; }
+// FP64 runs at a small fraction of the FP32 rate on GB300, so an FP64 product
+// takes as long as its busiest SM: up to np = 1024 it uses 16 x 16 tiles (136
+// upper tiles at np = 256, where 64 x 64 tiles would keep 10 SMs busy and leave
+// the rest idle), above that 64 x 64.
+void simt_tile_shape(int mode, int64_t np, int* bm, int* bn) {
+  if (mode == SP2_MODE_FP64) {
+    const int t = np <= 1024 ? 16 : 64;
+    *bm = t;
+    *bn = t;
+  } else {
+    *bm = 128;
+    *bn = 128;
+  }
 }
 
 cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, const void* X,
@@ -145,7 +155,13 @@ cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, c
                              cudaStream_t s) {
   (void)a_rows;
   if (ntiles <= 0) return cudaSuccess;
-  if (mode == SP2_MODE_FP64) {
+  int bm, bn;
+  simt_tile_shape(mode, np, &bm, &bn);
+  if (mode == SP2_MODE_FP64 && bm == 16) {
+    k_gemm_simt<double, 16, 16, 32, 1, 1><<<ntiles, 256, 0, s>>>(
+        static_cast<const double*>(A), static_cast<const double*>(X), np, epi,
+        static_cast<double*>(out), static_cast<const double*>(x_prev), part, tiles, st, step);
+  } else if (mode == SP2_MODE_FP64) {
     k_gemm_simt<double, 64, 64, 8, 4, 4><<<ntiles, 256, 0, s>>>(
         static_cast<const double*>(A), static_cast<const double*>(X), np, epi,
         static_cast<double*>(out), static_cast<const double*>(x_prev), part, tiles, st, step);

@@ -64,6 +64,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "sp2_internal.h"
 
 namespace sp2 {
@@ -1103,6 +1105,49 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t np, int bo
   return r == CUDA_SUCCESS;
 }
 
+// The tensor maps of a launch are a function of its plane addresses, shapes and
+// box sizes alone, and a solve uses a handful of such combinations (the two X
+// buffers, the response buffers), so they are encoded once and reused: encoding
+// the twelve maps of a launch anew cost tens of microseconds of host time per
+// step, which bounds the step rate of small problems. A small table, replaced
+// round robin, shared by every thread of the process.
+struct MapKey {
+  const void* planes[6];
+  int64_t prows, qrows, np;
+  int cg, f16;
+};
+
+bool cached_maps(const MapKey& k, KMaps* out) {
+  constexpr int kSlots = 32;
+  static std::mutex mu;
+  static MapKey keys[kSlots];
+  static KMaps maps[kSlots];
+  static bool used[kSlots] = {};
+  static int next = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < kSlots; ++i)
+    if (used[i] && memcmp(&keys[i], &k, sizeof k) == 0) {
+      *out = maps[i];
+      return true;
+    }
+  KMaps m;
+  bool ok = true;
+  for (int i = 0; i < 3; ++i) {
+    ok = ok && make_map(&m.pa[i], k.planes[i], k.prows, k.np, BM, k.f16) &&
+         make_map(&m.qb[i], k.planes[3 + i], k.qrows, k.np, BN / k.cg, k.f16);
+    // EPI_SYMM's second half reads X as the left and Y as the right factor
+    ok = ok && make_map(&m.qa[i], k.planes[3 + i], k.qrows, k.np, BM, k.f16) &&
+         make_map(&m.pb[i], k.planes[i], k.prows, k.np, BN / k.cg, k.f16);
+  }
+  if (!ok) return false;
+  keys[next] = k;
+  maps[next] = m;
+  used[next] = true;
+  next = (next + 1) % kSlots;
+  *out = m;
+  return true;
+}
+
 // one launch of the (KIND, EPI, CG) kernel over `units` CTAs or CTA pairs (at most
 // the resident ones), with its shared-memory attribute and its resident-pair
 // count queried once
@@ -1223,17 +1268,20 @@ cudaError_t launch_gemm_tc(const TcLaunch& L, cudaStream_t s, char* errbuf, size
     return cudaErrorInvalidValue;
   }
   KMaps maps;
-  const uint16_t* pp[3] = {P.hi, P.lo, p_mid};
-  const uint16_t* qq[3] = {Q.hi, Q.lo, q_mid};
-  bool mapped = true;
-  for (int i = 0; i < 3; ++i) {
-    mapped = mapped && make_map(&maps.pa[i], pp[i], P.rows, np, BM, f16) &&
-             make_map(&maps.qb[i], qq[i], Q.rows, np, BN / cg, f16);
-    // EPI_SYMM's second half reads X as the left and Y as the right factor
-    mapped = mapped && make_map(&maps.qa[i], qq[i], Q.rows, np, BM, f16) &&
-             make_map(&maps.pb[i], pp[i], P.rows, np, BN / cg, f16);
-  }
-  if (!mapped) {
+  MapKey key;
+  memset(&key, 0, sizeof key);   // padding bytes too: the key is compared bytewise
+  key.planes[0] = P.hi;
+  key.planes[1] = P.lo;
+  key.planes[2] = p_mid;
+  key.planes[3] = Q.hi;
+  key.planes[4] = Q.lo;
+  key.planes[5] = q_mid;
+  key.prows = P.rows;
+  key.qrows = Q.rows;
+  key.np = np;
+  key.cg = cg;
+  key.f16 = f16 ? 1 : 0;
+  if (!cached_maps(key, &maps)) {
     snprintf(errbuf, errlen, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     return cudaErrorInvalidValue;
   }

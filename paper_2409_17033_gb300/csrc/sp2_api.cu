@@ -236,9 +236,9 @@ int join_beside(sp2_handle_t h) {
 size_t dsize(int dtype) { return dtype == SP2_F64 ? 8 : 4; }
 
 // --------------------------------------------------------------- tile lists
-void tile_shape(sp2_handle_t h, int mode, int* bm, int* bn) {
+void tile_shape(sp2_handle_t h, int mode, int64_t np, int* bm, int* bn) {
   if (split_mode(mode)) tc_tile_shape(h->tune.pair, bm, bn);
-  else simt_tile_shape(mode, bm, bn);
+  else simt_tile_shape(mode, np, bm, bn);
 }
 
 // partials per output tile: a CTA pair's two CTAs each report their own rows
@@ -251,7 +251,7 @@ int parts_per_tile(sp2_handle_t h, int mode) { return split_mode(mode) && h->tun
 int tile_list(sp2_handle_t h, int mode, int64_t rows, int64_t np, bool upper, const Tile** d,
               int* n) {
   int bm, bn;
-  tile_shape(h, mode, &bm, &bn);
+  tile_shape(h, mode, np, &bm, &bn);
   char key[96];
   snprintf(key, sizeof key, "%d/%lld/%lld/%d/%dx%d", mode, (long long)rows, (long long)np,
            (int)upper, bm, bn);
@@ -355,7 +355,7 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
   int nt;
   TRY(tile_list(h, c.mode, c.np, c.np, true, &tl, &nt));
   int bm, bn;
-  tile_shape(h, c.mode, &bm, &bn);
+  tile_shape(h, c.mode, c.np, &bm, &bn);
   TcLaunch L;   // workspace first: nothing is allocated inside the timed interval
   if (split_mode(c.mode)) TRY(tc_common(c, &L, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -473,7 +473,7 @@ int response_step(Ctx& c, const MatBuf& x, const MatBuf& yin, const MatBuf& yout
   int nt;
   TRY(tile_list(h, c.mode, rows, c.np, fused, &tl, &nt));
   int bm, bn;
-  tile_shape(h, c.mode, &bm, &bn);
+  tile_shape(h, c.mode, c.np, &bm, &bn);
   // workspace first: nothing is allocated inside the timed interval
   TcLaunch L;
   void* yp = nullptr;
@@ -694,7 +694,7 @@ struct Sp2Out {
 int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, const sp2_opts& o,
             const void* Bd, int64_t ybatch, int b_diag, bool keep, MatBuf X[2], MatBuf Y[2],
             Ctx& c, Sp2Out* out) {
-  const int64_t np = pad_n(n);
+  const int64_t np = c.np;   // the caller's padding (one for every mode a loop may switch to)
   const int mode = o.mode;
   const bool sparse = o.block_sparse != 0;
   if (sparse) {
@@ -929,7 +929,7 @@ int make_ctx(sp2_handle_t h, int mode, int64_t n, int64_t np, bool timing, Ctx* 
   c->timing = timing;
   c->st = h->d_state;
   int bm, bn;
-  tile_shape(h, mode, &bm, &bn);
+  tile_shape(h, mode, np, &bm, &bn);
   int64_t maxp = (np / bm) * (np / bn) * parts_per_tile(h, mode) + 8;
   if (maxp < init_nparts(np)) maxp = init_nparts(np);
   void* p;
@@ -1182,7 +1182,7 @@ int fprod(Ctx& c, FMat& C, const FMat& L, const FMat& R) {
   int nt;
   TRY(tile_list(h, c.mode, c.np, c.np, false, &tl, &nt));
   int bm, bn;
-  tile_shape(h, c.mode, &bm, &bn);
+  tile_shape(h, c.mode, c.np, &bm, &bn);
   TcLaunch T;   // workspace first: nothing is allocated inside the timed interval
   if (split_mode(c.mode)) TRY(tc_common(c, &T, nt));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1384,7 +1384,7 @@ int sp2_density(sp2_handle_t h, const void* H, int64_t N, int dtype, double nocc
   TRY(stage_in(h, "H", H, mb, &Hd));
   OutStage od;
   TRY(stage_out(h, "D", D, mb, &od));
-  const int64_t np = pad_n(N);
+  const int64_t np = pad_n(N, o.mode);
   Ctx c;
   TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
   MatBuf X[2], Y[2];
@@ -1433,7 +1433,7 @@ int sp2_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double noc
   OutStage od, oy;
   if (D) TRY(stage_out(h, "D", D, mb, &od));
   if (K > 0) TRY(stage_out(h, "Y", D1, (size_t)K * mb, &oy));
-  const int64_t np = pad_n(N);
+  const int64_t np = pad_n(N, o.mode);
   Ctx c;
   TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
   MatBuf X[2], Y[2];
@@ -1487,7 +1487,7 @@ int sp2_susceptibility(sp2_handle_t h, const void* H, int64_t N, int dtype, doub
   OutStage od, oy;
   if (D) TRY(stage_out(h, "D", D, mb, &od));
   if (L > 0) TRY(stage_out(h, "Y", chi, (size_t)L * mb, &oy));
-  const int64_t np = pad_n(N);
+  const int64_t np = pad_n(N, o.mode);
   Ctx c;
   TRY(make_ctx(h, o.mode, N, np, o.time_kernels != 0, &c));
   MatBuf X[2], Y[2];
@@ -1758,7 +1758,7 @@ int sp2_fermi(sp2_handle_t h, const void* H, int64_t N, int dtype, double mu, do
     return SP2_OK;
   }
   const int mode = o.mode;
-  const int64_t np = pad_n(N);
+  const int64_t np = pad_n(N, mode);
   const size_t mb = (size_t)N * N * dsize(dtype);
   const void *Hd, *Bd = nullptr;
   TRY(stage_in(h, "H", H, mb, &Hd));
@@ -1868,7 +1868,7 @@ int sp2_nonorth_susceptibility(sp2_handle_t h, const void* H, const void* S, int
     return SP2_OK;
   }
   const int mode = o.mode;
-  const int64_t np = pad_n(N);
+  const int64_t np = pad_n(N, mode);
   const size_t mb = (size_t)N * N * dsize(dtype);
   const void *Hd, *Sd, *Ad;
   TRY(stage_in(h, "H", H, mb, &Hd));
@@ -2223,7 +2223,8 @@ int sp2_scf_response(sp2_handle_t h, const void* H, int64_t N, int dtype, double
       so->refine_mode != SP2_MODE_BF16X3)
     return fail(h, SP2_EINVAL, "unknown refine_mode %d", so->refine_mode);
   if (info) memset(info, 0, sizeof *info);
-  const int64_t ns = N / norb, np = pad_n(N), tot = F * ns;
+  // one padding for every mode the loop may switch to (the split modes' 256)
+  const int64_t ns = N / norb, np = pad_n(N, SP2_MODE_FP16X2), tot = F * ns;
   const size_t mb = (size_t)N * N * dsize(dtype);
   const void *Hd, *Kd, *Vd;
   TRY(stage_in(h, "H", H, mb, &Hd));

@@ -12,12 +12,18 @@
 
 namespace sp2 {
 
-// Internal matrices are padded to a multiple of this (the largest tile edge),
-// zero outside the caller's N x N block. Zero padding is invariant under all
-// recursions (X -> X^2, 2X - X^2, Y -> YX + XY), so it never touches results.
+// Internal matrices are padded to a multiple of the largest tile edge of their
+// arithmetic mode, zero outside the caller's N x N block: 256 for the split
+// modes (the tensor-core tiles and the TMA row pitch), 128 for FP32 (its
+// CUDA-core tiles), 64 for FP64 (its tiles; GB300's FP64 rate makes every padded
+// row count). Zero padding is invariant under all recursions (X -> X^2,
+// 2X - X^2, Y -> YX + XY), so it never touches results.
 constexpr int kPad = 256;
 
-inline int64_t pad_n(int64_t n) { return (n + kPad - 1) / kPad * kPad; }
+inline int64_t pad_n(int64_t n, int mode) {
+  const int64_t q = mode == SP2_MODE_FP64 ? 64 : (mode == SP2_MODE_FP32 ? 128 : kPad);
+  return (n + q - 1) / q * q;
+}
 
 // Device-resident SP2 control state: traces of every X_n, the branch signs
 // and the stop decision. Written only by k_decide; read by the step kernels
@@ -206,7 +212,7 @@ cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, c
                              int64_t np, void* out, const void* x_prev, Part3* part,
                              const Tile* tiles, int ntiles, const DevState* st, int step,
                              cudaStream_t s);
-void simt_tile_shape(int mode, int* bm, int* bn);
+void simt_tile_shape(int mode, int64_t np, int* bm, int* bn);
 
 // tcgen05 split-precision (BF16X2 / FP16X2 / BF16X3)
 struct TcOperand {   // hi/lo (and BF16X3 mid) planes of a stacked operand, rows x np
