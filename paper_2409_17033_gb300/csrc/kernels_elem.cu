@@ -492,15 +492,54 @@ __device__ __forceinline__ void store_planes4(MatBuf d, int mode, int64_t t, con
   if (mode == SP2_MODE_BF16X3) reinterpret_cast<uint2*>(d.mid)[t] = pack4(md);
 }
 
-// X_1 = alpha I + beta H (coefficients from st) with its planes: the same stored
-// values as k_init (beta h + alpha in FP64, rounded once); the trace partials
-// add the squares of four stored entries in FP32 before FP64
+// FP32 forms of FP64 arithmetic for the O(N^2) passes (GB300's FP64 pipe, and
+// its conversions, run at a small fraction of the FP32 rate and bounded these
+// passes well below the HBM bandwidth):
+// - TwoSum (Knuth) and the fmaf product residual give an addition's and a
+//   product's rounding error exactly; the _rn intrinsics keep the compiler from
+//   contracting the steps into fused operations, which would lose them;
+// - an FP64 coefficient c is carried as hi + lo, hi = fl32(c), lo = fl32(c - hi),
+//   and x c is formed as fl32(p + (e + x lo)) with p = fl32(x hi) and e its
+//   residual: within one rounding of the exact x c (the FP64 form rounds twice).
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 split_coef(double c) {
+  const float hi = (float)c;
+  return F2{hi, (float)(c - (double)hi)};
+}
+__device__ __forceinline__ float mul_coef(float x, F2 c) {
+  const float p = __fmul_rn(x, c.hi);
+  const float e = fmaf(x, c.hi, -p);
+  return __fadd_rn(p, fmaf(x, c.lo, e));
+}
+// s + c += x with the rounding error of the addition carried in c
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+  s = t;
+}
+// s + c += x^2 exactly up to the rounding of c
+__device__ __forceinline__ void two_sum_add_sq(float& s, float& c, float x) {
+  const float p = __fmul_rn(x, x);
+  two_sum_add(s, c, p);
+  c = __fadd_rn(c, fmaf(x, x, -p));
+}
+
+// X_1 = alpha I + beta H (coefficients from st) with its planes. Off the diagonal
+// an entry is beta h formed in FP32 from beta = hi + lo (mul_coef); a diagonal
+// entry, one per row, is beta h + alpha in FP64, rounded once. The trace partials
+// take Tr exactly (the diagonal entries) and ||X_1||_F^2 as an exact FP32 sum of
+// squares per row segment, added in FP64.
 __global__ void k_init_x4(const float* __restrict__ src, int64_t n, int64_t np, int mode,
                           MatBuf dst, Part3* part, const DevState* st) {
   const double alpha = st->alpha, beta = st->beta;
+  const F2 bc = split_coef(beta);
   double t1 = 0.0, t2 = 0.0;
   const int64_t q = np / 4;
   for (int64_t r = blockIdx.x; r < np; r += gridDim.x) {
+    float ss = 0.0f, sc = 0.0f;   // this thread's sum of squares of the row segment
     for (int64_t c = threadIdx.x; c < q; c += blockDim.x) {
       const int64_t j = 4 * c;
       float x[4] = {0.f, 0.f, 0.f, 0.f};
@@ -513,16 +552,17 @@ __global__ void k_init_x4(const float* __restrict__ src, int64_t n, int64_t np, 
       }
       float f[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        double v = (r < n && j + k < n) ? beta * (double)x[k] : 0.0;
-        if (r < n && j + k == r) v += alpha;
-        f[k] = (float)v;
+      for (int k = 0; k < 4; ++k) f[k] = mul_coef(x[k], bc);
+      if (r < n && r >= j && r < j + 4) {
+        f[r - j] = (float)(beta * (double)x[r - j] + alpha);
+        t1 += (double)f[r - j];
       }
       reinterpret_cast<float4*>(dst.master)[r * q + c] = make_float4(f[0], f[1], f[2], f[3]);
       store_planes4(dst, mode, r * q + c, f);
-      t2 += (double)(f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3]);
-      if (r >= j && r < j + 4) t1 += (double)f[r - j];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) two_sum_add_sq(ss, sc, f[k]);
     }
+    t2 += (double)ss + (double)sc;
   }
   t1 = block_sum(t1);
   __syncthreads();
@@ -530,22 +570,32 @@ __global__ void k_init_x4(const float* __restrict__ src, int64_t n, int64_t np, 
   if (threadIdx.x == 0) part[blockIdx.x] = Part3{t1, t2, 0.0};
 }
 
-// Gershgorin discs of an FP32 H, one warp per row (FP64 row sums)
+// Gershgorin discs of an FP32 H, one warp per row: each lane sums |h| of its
+// part of the row with TwoSum in FP32 and moves the sum and its error to FP64
+// every 32 entries; lanes add in FP64.
 __global__ void k_bounds_x4(const float* __restrict__ H, int64_t n, double2* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double lo = INFINITY, hi = -INFINITY;
   for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
     const float* row = H + i * n;
     double r = 0.0, d = 0.0;
+    float s = 0.0f, e = 0.0f;
+    int cnt = 0;
     for (int64_t c = lane; c < n / 4; c += 32) {
       const float4 h = *reinterpret_cast<const float4*>(row + 4 * c);
       const float x[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (4 * c + k == i) d = x[k];
-        else r += fabs((double)x[k]);
+        else two_sum_add(s, e, fabsf(x[k]));
+      }
+      if (++cnt == 8) {
+        r += (double)s + (double)e;
+        s = e = 0.0f;
+        cnt = 0;
       }
     }
+    r += (double)s + (double)e;
     for (int o = 16; o > 0; o >>= 1) {
       r += __shfl_xor_sync(0xffffffffu, r, o);
       d += __shfl_xor_sync(0xffffffffu, d, o);
@@ -559,23 +609,29 @@ __global__ void k_bounds_x4(const float* __restrict__ H, int64_t n, double2* par
   if (threadIdx.x == 0) part[blockIdx.x] = mm;
 }
 
-// caller-layout copy of an FP32 master, four entries per step; the same values
-// as k_copy_out (FP64 product with the scale, rounded once) when scaled
+// caller-layout copy of an FP32 master, four entries per step, one row per block
+// step (no per-entry division); a scale (times beta from the state, when given)
+// is applied as an FP32 product with the split coefficient (mul_coef)
 __global__ void k_copy_out_x4(const float* __restrict__ src, int64_t n, int64_t np, int64_t batch,
                               double scale, float* __restrict__ dst, const DevState* beta_state) {
   if (beta_state) scale *= beta_state->beta;
-  const int64_t q = n / 4, per = n * q, total = batch * per;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = t / per, rem = t % per, i = rem / q, c = rem % q;
-    float4 v = *reinterpret_cast<const float4*>(src + (b * np + i) * np + 4 * c);
-    if (scale != 1.0) {
-      v.x = (float)((double)v.x * scale);
-      v.y = (float)((double)v.y * scale);
-      v.z = (float)((double)v.z * scale);
-      v.w = (float)((double)v.w * scale);
+  const bool scaled = scale != 1.0;
+  const F2 sc = split_coef(scale);
+  const int64_t q = n / 4, rows = batch * n;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int64_t b = row / n, i = row - b * n;
+    const float4* s4 = reinterpret_cast<const float4*>(src + (b * np + i) * np);
+    float4* d4 = reinterpret_cast<float4*>(dst) + row * q;
+    for (int64_t c = threadIdx.x; c < q; c += blockDim.x) {
+      float4 v = s4[c];
+      if (scaled) {
+        v.x = mul_coef(v.x, sc);
+        v.y = mul_coef(v.y, sc);
+        v.z = mul_coef(v.z, sc);
+        v.w = mul_coef(v.w, sc);
+      }
+      d4[c] = v;
     }
-    reinterpret_cast<float4*>(dst)[t] = v;
   }
 }
 
@@ -866,7 +922,7 @@ cudaError_t launch_copy_out(MatBuf src, int64_t n, int64_t np, int64_t batch, in
                             const DevState* beta_state) {
   if (mode != SP2_MODE_FP64 && dtype == SP2_F32 && n % 4 == 0 &&
       (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
-    k_copy_out_x4<<<grid_for(batch * n * n / 4, 256, 8192), 256, 0, s>>>(
+    k_copy_out_x4<<<grid_for(batch * n, 1, 8192), 256, 0, s>>>(
         static_cast<const float*>(src.master), n, np, batch, scale, static_cast<float*>(dst),
         beta_state);
     return cudaGetLastError();
