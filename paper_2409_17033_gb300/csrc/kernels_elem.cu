@@ -571,31 +571,36 @@ __global__ void k_init_x4(const float* __restrict__ src, int64_t n, int64_t np, 
 }
 
 // Gershgorin discs of an FP32 H, one warp per row: each lane sums |h| of its
-// part of the row with TwoSum in FP32 and moves the sum and its error to FP64
-// every 32 entries; lanes add in FP64.
+// part of the row with TwoSum in FP32, four 16-byte loads in flight, and moves
+// the sum and its error to FP64 after each group of 16 entries; lanes add in FP64.
 __global__ void k_bounds_x4(const float* __restrict__ H, int64_t n, double2* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t q = n / 4;
   double lo = INFINITY, hi = -INFINITY;
   for (int64_t i = (int64_t)blockIdx.x * nw + warp; i < n; i += (int64_t)gridDim.x * nw) {
-    const float* row = H + i * n;
+    const float4* row = reinterpret_cast<const float4*>(H + i * n);
+    const int64_t cd = i >> 2;   // the group holding the diagonal entry
     double r = 0.0, d = 0.0;
-    float s = 0.0f, e = 0.0f;
-    int cnt = 0;
-    for (int64_t c = lane; c < n / 4; c += 32) {
-      const float4 h = *reinterpret_cast<const float4*>(row + 4 * c);
-      const float x[4] = {h.x, h.y, h.z, h.w};
+    for (int64_t c0 = lane; c0 < q; c0 += 4 * 32) {
+      float4 h[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (4 * c + k == i) d = x[k];
-        else two_sum_add(s, e, fabsf(x[k]));
+      for (int u = 0; u < 4; ++u) {
+        const int64_t c = c0 + 32 * u;
+        h[u] = c < q ? row[c] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      if (++cnt == 8) {
-        r += (double)s + (double)e;
-        s = e = 0.0f;
-        cnt = 0;
+      float s = 0.0f, e = 0.0f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float x[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
+        if (c0 + 32 * u == cd) {   // take the diagonal entry out of the row sum
+          d = x[i & 3];
+          x[i & 3] = 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) two_sum_add(s, e, fabsf(x[k]));
       }
+      r += (double)s + (double)e;
     }
-    r += (double)s + (double)e;
     for (int o = 16; o > 0; o >>= 1) {
       r += __shfl_xor_sync(0xffffffffu, r, o);
       d += __shfl_xor_sync(0xffffffffu, d, o);
