@@ -772,20 +772,8 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
       for (int it = 0; it < my_tiles && ok; ++it) {
         const Tile t = p.tiles[unit + it * nunits];
         const int bat = (int)(t.row0 / np);
-        int seg = 0, kin = -1;   // segment of k-block kb and its k-block within the segment
-        for (int kb = 0; kb < total_kb; ++kb, ++g, rp.next()) {
-          if (++kin == nkb) {
-            kin = 0;
-            ++seg;
-          }
-          const int s = rp.s;
-          const uint32_t ph = rp.ph;
-          if (!mbar_wait<PAIR>(&empty[s], ph ^ 1u, abortf, p.wait_ns)) {
-            ok = false;
-            break;
-          }
-          if (p.withhold && blockIdx.x == 0 && g == 0) continue;  // test hook: never completes
-          const int kx = kin * BK;
+        for (int seg = 0; seg < nseg && ok; ++seg) {
+          // the segment's operands and tile rows, fixed over its k-blocks
           const bool swap = EPI == EPI_SYMM && seg >= nbase;   // second half: [Q | .] . [. ; P]
           int pa, pb;
           seg_planes<KIND>(swap ? seg - nbase : seg, nbase, pa, pb);
@@ -795,10 +783,18 @@ k_gemm_tc(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p)
           // of the B tile (one CTA: all of both)
           const int arow = (swap ? t.row0 - bat * (int)np : t.row0) + (int)rank * BM;
           const int brow = (swap ? bat * (int)np + t.col0 : t.col0) + (int)rank * R::B_ROWS;
-          uint8_t* sa = smem + s * STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-          tma_load_2d(ma, &full[s], sa, kx, arow);
-          tma_load_2d(mb, &full[s], sa + A_BYTES, kx, brow);
+          for (int kx = 0; kx < nkb * BK; kx += BK, ++g, rp.next()) {
+            const int s = rp.s;
+            if (!mbar_wait<PAIR>(&empty[s], rp.ph ^ 1u, abortf, p.wait_ns)) {
+              ok = false;
+              break;
+            }
+            if (p.withhold && blockIdx.x == 0 && g == 0) continue;  // test hook: never completes
+            uint8_t* sa = smem + s * STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(ma, &full[s], sa, kx, arow);
+            tma_load_2d(mb, &full[s], sa + A_BYTES, kx, brow);
+          }
         }
       }
       if (!ok) {
