@@ -107,14 +107,26 @@ typedef enum { SP2_F64 = 0, SP2_F32 = 1 } sp2_dtype;
  *                    lo*hi): the multi-split extension of Eq. MixPrecMult
  *                    that Sec. VI.C names for tunable accuracy; twice the
  *                    tensor work of the two-plane modes, no scaling.
+ *   SP2_MODE_BF16_TAIL  the bfloat16-bulk / split-tail form of Sec. VI.B (tensor-
+ *                    core results as the start of higher-precision work in the
+ *                    last iterations): SP2_MODE_BF16X2 with the split-tail option
+ *                    (sp2_opts.tail_f, below) on; tail_f = 0 takes
+ *                    SP2_DEFAULT_TAIL_F. The calls run and report it as
+ *                    SP2_MODE_BF16X2 with that tail_f. Its density error is set by
+ *                    the bulk's bfloat16 rounding times the condition number (the
+ *                    split tail restores idempotency, not the subspace).
  */
 typedef enum {
   SP2_MODE_FP64 = 0,
   SP2_MODE_FP32 = 1,
   SP2_MODE_BF16X2 = 2,
   SP2_MODE_FP16X2 = 3,
-  SP2_MODE_BF16X3 = 4
+  SP2_MODE_BF16X3 = 4,
+  SP2_MODE_BF16_TAIL = 5
 } sp2_mode;
+
+/* tail_f of SP2_MODE_BF16_TAIL when the caller leaves it at 0 */
+#define SP2_DEFAULT_TAIL_F 1.0
 
 typedef struct {
   int mode;            /* sp2_mode */

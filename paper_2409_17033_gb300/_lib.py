@@ -23,9 +23,10 @@ STATUS_NAMES = {0: "SP2_OK", 1: "SP2_EINVAL", 2: "SP2_ENOMEM", 3: "SP2_ENOCONV",
 # sp2_dtype
 F64, F32 = 0, 1
 # sp2_mode
-MODE_FP64, MODE_FP32, MODE_BF16X2, MODE_FP16X2, MODE_BF16X3 = 0, 1, 2, 3, 4
+MODE_FP64, MODE_FP32, MODE_BF16X2, MODE_FP16X2, MODE_BF16X3, MODE_BF16_TAIL = 0, 1, 2, 3, 4, 5
 MODES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16x2": MODE_BF16X2, "fp16x2": MODE_FP16X2,
-         "bf16x3": MODE_BF16X3}
+         "bf16x3": MODE_BF16X3, "bf16_tail": MODE_BF16_TAIL}
+DEFAULT_TAIL_F = 1.0   # SP2_DEFAULT_TAIL_F
 CKPT_AUTO = -1   # SP2_CKPT_AUTO
 # sp2_option
 OPTION_WAIT_LIMIT_NS, OPTION_WITHHOLD_LOAD, OPTION_FUSED_RESPONSE, OPTION_PAIR_TILES = 0, 1, 2, 3

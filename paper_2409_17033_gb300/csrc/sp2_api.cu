@@ -631,6 +631,11 @@ sp2_opts resolve(const sp2_opts* in) {
   if (o.min_iter < 0) o.min_iter = 4;
   if (o.floor_gate < 0) o.floor_gate = 0.03;
   if (o.ckpt_k == 0) o.ckpt_k = 4;
+  // the named bfloat16-bulk / split-tail mode is BF16X2 with the split tail on
+  if (o.mode == SP2_MODE_BF16_TAIL) {
+    o.mode = SP2_MODE_BF16X2;
+    if (o.tail_f == 0.0) o.tail_f = SP2_DEFAULT_TAIL_F;
+  }
   return o;
 }
 

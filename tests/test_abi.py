@@ -130,3 +130,26 @@ def test_info_dict_fields(lib):
     from paper_2409_17033_gb300 import _lib
     d = _lib.Info().to_dict()
     assert "ckpt_k" in d and "refine_iter" in d
+
+
+def test_mode_constants_match_the_header(tmp_path, lib):
+    """The binding's mode numbers and SP2_DEFAULT_TAIL_F are the header's."""
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2409_17033_gb300 import _lib
+    probe = tmp_path / "modes.c"
+    names = ["SP2_MODE_FP64", "SP2_MODE_FP32", "SP2_MODE_BF16X2", "SP2_MODE_FP16X2",
+             "SP2_MODE_BF16X3", "SP2_MODE_BF16_TAIL"]
+    lines = ['#include <stdio.h>', f'#include "{HEADER}"', "int main(void){"]
+    lines += [f'printf("%d\\n", (int){n});' for n in names]
+    lines += ['printf("%.17g\\n", (double)SP2_DEFAULT_TAIL_F);', "return 0;}"]
+    probe.write_text("\n".join(lines))
+    exe = tmp_path / "modes"
+    subprocess.run([gcc, str(probe), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = [int(x) for x in out[:-1]]
+    assert got == [_lib.MODE_FP64, _lib.MODE_FP32, _lib.MODE_BF16X2, _lib.MODE_FP16X2,
+                   _lib.MODE_BF16X3, _lib.MODE_BF16_TAIL]
+    assert [_lib.MODES[k] for k in ("fp64", "fp32", "bf16x2", "fp16x2", "bf16x3", "bf16_tail")] == got
+    assert float(out[-1]) == _lib.DEFAULT_TAIL_F

@@ -96,3 +96,21 @@ def test_zero_threshold_is_the_split_mode(sp2, c1):
                                           want_density=True, tail_f=0.0)
     assert i1["tail_single_steps"] == 0 and i0["sigma"] == i1["sigma"]
     assert torch.equal(chi0, chi1) and torch.equal(D0, D1)
+
+
+def test_named_bf16_tail_mode_is_bf16x2_with_the_split_tail(sp2, c1):
+    """SP2_MODE_BF16_TAIL (the boundary's bfloat16-bulk / split-tail mode) is
+    BF16X2 with tail_f = SP2_DEFAULT_TAIL_F unless tail_f is given: bit for bit
+    the same results, and single-plane steps in the bulk only."""
+    from paper_2409_17033_gb300 import _lib
+    p = c1
+    H, A = f32(p.H), f32(p.A[None])
+    for tf in (0.0, 1e-2):
+        chi_n, D_n, i_n = sp2.sp2_susceptibility(H, p.nocc, A, "backward", mode="bf16_tail",
+                                                 want_density=True, tail_f=tf)
+        chi_x, D_x, i_x = sp2.sp2_susceptibility(H, p.nocc, A, "backward", mode="bf16x2",
+                                                 want_density=True,
+                                                 tail_f=tf if tf > 0 else _lib.DEFAULT_TAIL_F)
+        assert i_n["converged"] and 0 < i_n["tail_single_steps"] < i_n["M"]
+        assert i_n["sigma"] == i_x["sigma"] and i_n["tail_single_steps"] == i_x["tail_single_steps"]
+        assert torch.equal(chi_n, chi_x) and torch.equal(D_n, D_x)
