@@ -9,6 +9,7 @@
 //               symmetric. Per-block FP64 partials of Tr[X] and ||X||_F^2.
 //   EPI_PLAIN   Z = A X for the response update of Eqs. DM1-DM3.
 #include "sp2_internal.h"
+#include "decide.cuh"
 
 namespace sp2 {
 
@@ -27,7 +28,7 @@ template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(256)
 k_gemm_simt(const T* __restrict__ A, const T* __restrict__ X, int64_t np, int epi,
             T* __restrict__ out, const T* __restrict__ xprev, Part3* __restrict__ part,
-            const Tile* __restrict__ tiles, const DevState* st, int step) {
+            const Tile* __restrict__ tiles, const DevState* st, int step, SimtDecide dec) {
   static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
   using V = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
@@ -130,6 +131,21 @@ k_gemm_simt(const T* __restrict__ A, const T* __restrict__ X, int64_t np, int ep
     for (int w = 0; w < 8; ++w) { s1 += r1[w]; s2 += r2[w]; s3 += r3[w]; }
     part[blockIdx.x] = Part3{s1, s2, s3};
   }
+  if (dec.done) {
+    // the last block to finish reduces every block's partials (fixed order, as the
+    // decision kernel does) and takes the step decision
+    __shared__ int last;
+    if (tid == 0) {
+      __threadfence();
+      last = atomicAdd(dec.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      decide_block(part, dec.st, dec.p);
+      if (tid == 0) *dec.done = 0u;
+    }
+  }
 }
 
 }  // namespace
@@ -152,23 +168,25 @@ void simt_tile_shape(int mode, int64_t np, int* bm, int* bn) {
 cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, const void* X,
                              int64_t np, void* out, const void* x_prev, Part3* part,
                              const Tile* tiles, int ntiles, const DevState* st, int step,
-                             cudaStream_t s) {
+                             cudaStream_t s, const SimtDecide* dec) {
   (void)a_rows;
   if (ntiles <= 0) return cudaSuccess;
   int bm, bn;
   simt_tile_shape(mode, np, &bm, &bn);
+  SimtDecide sd;
+  if (dec && epi == EPI_SQUARE) sd = *dec;
   if (mode == SP2_MODE_FP64 && bm == 16) {
     k_gemm_simt<double, 16, 16, 32, 1, 1><<<ntiles, 256, 0, s>>>(
         static_cast<const double*>(A), static_cast<const double*>(X), np, epi,
-        static_cast<double*>(out), static_cast<const double*>(x_prev), part, tiles, st, step);
+        static_cast<double*>(out), static_cast<const double*>(x_prev), part, tiles, st, step, sd);
   } else if (mode == SP2_MODE_FP64) {
     k_gemm_simt<double, 64, 64, 8, 4, 4><<<ntiles, 256, 0, s>>>(
         static_cast<const double*>(A), static_cast<const double*>(X), np, epi,
-        static_cast<double*>(out), static_cast<const double*>(x_prev), part, tiles, st, step);
+        static_cast<double*>(out), static_cast<const double*>(x_prev), part, tiles, st, step, sd);
   } else {
     k_gemm_simt<float, 128, 128, 8, 8, 8><<<ntiles, 256, 0, s>>>(
         static_cast<const float*>(A), static_cast<const float*>(X), np, epi,
-        static_cast<float*>(out), static_cast<const float*>(x_prev), part, tiles, st, step);
+        static_cast<float*>(out), static_cast<const float*>(x_prev), part, tiles, st, step, sd);
   }
   return cudaGetLastError();
 }

@@ -348,8 +348,11 @@ int tc_common(Ctx& c, TcLaunch* L, int ntiles) {
   return SP2_OK;
 }
 
-// X_{n+1} = sigma_n>0 ? X_n^2 : 2 X_n - X_n^2, with trace partials; returns #partials
-int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* nparts) {
+// X_{n+1} = sigma_n>0 ? X_n^2 : 2 X_n - X_n^2, with trace partials; returns #partials.
+// dec (CUDA-core modes): the step decision with these parameters is taken by the
+// product's last block instead of a separate launch (dec->nparts is set here).
+int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* nparts,
+                const DecideParams* dec = nullptr) {
   sp2_handle_t h = c.h;
   const Tile* tl;
   int nt;
@@ -375,8 +378,17 @@ int square_step(Ctx& c, const MatBuf& xin, const MatBuf& xout, int step, int* np
     cudaError_t e = launch_gemm_tc(L, h->stream, eb, sizeof eb);
     if (e != cudaSuccess) return fail(h, SP2_ECUDA, "square product: %s %s", cudaGetErrorString(e), eb);
   } else {
+    SimtDecide sd;
+    if (dec) {
+      void* dn;
+      TRY(ws(h, "decide.done", sizeof(unsigned), &dn));
+      sd.p = *dec;
+      sd.p.nparts = nt;
+      sd.st = c.st;
+      sd.done = static_cast<unsigned*>(dn);
+    }
     CK(launch_gemm_simt(c.mode, EPI_SQUARE, xin.master, c.np, xin.master, c.np, xout.master,
-                        xin.master, c.part, tl, nt, c.st, step, h->stream));
+                        xin.master, c.part, tl, nt, c.st, step, h->stream, dec ? &sd : nullptr));
   }
   if (c.timing) {
     CK(cudaEventRecord(e1, h->stream));
@@ -794,6 +806,12 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
     TRY(ws(h, "Xbest.m", xbytes, &xbest.master));
     if (ybatch > 0) TRY(ws(h, "Ybest.m", (size_t)ybatch * xbytes, &ybest.master));
   }
+  if (!split_mode(mode) && !sparse) {
+    // the completion counter of the squares' last-block decision starts at zero
+    void* dn;
+    TRY(ws(h, "decide.done", sizeof(unsigned), &dn));
+    CK(cudaMemsetAsync(dn, 0, sizeof(unsigned), h->stream));
+  }
   const DevState* seen = nullptr;   // latest snapshot read
   int last = 0;                     // last step enqueued
   for (int step = 1; step <= maxit; ++step) {
@@ -823,13 +841,19 @@ int run_sp2(sp2_handle_t h, const void* Hd, int64_t n, int dtype, double nocc, c
       CK(launch_zero_blocks(sb, xo, np, mode, c.st, step, 0, h->stream));
       c.kernels += 2;
       CK(launch_decide(sb.psum, c.st, dp, h->stream));
+      c.kernels++;
+    } else if (!split_mode(mode)) {
+      // CUDA-core square: its last block takes the decision
+      int nparts = 0;
+      TRY(square_step(c, xin, xo, step, &nparts, &dp));
+      dp.nparts = nparts;
     } else {
       int nparts = 0;
       TRY(square_step(c, xin, xo, step, &nparts));
       dp.nparts = nparts;
       CK(launch_decide(c.part, c.st, dp, h->stream));
+      c.kernels++;
     }
-    c.kernels++;
     if (track) {
       CK(launch_keep_best(xin.master, xbest.master, np * np, mode, c.st, step, h->stream));
       c.kernels++;

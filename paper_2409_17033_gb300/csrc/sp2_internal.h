@@ -207,11 +207,20 @@ cudaError_t launch_contract(const void* P, int64_t L, const void* Q, int64_t K, 
 int contract_nparts(int64_t n, int q_diag);
 
 // product kernels
+// The step decision taken by the last block of a CUDA-core square (one launch
+// fewer per step): its parameters, the state it writes, and a completion counter
+// that is zero between launches (the last block resets it).
+struct SimtDecide {
+  DecideParams p;
+  DevState* st = nullptr;
+  unsigned* done = nullptr;
+};
 // SIMT (FP64 / FP32): C = A * X with A rows x np (stacked), X np x np symmetric.
+// dec (squares only, may be null): take the step decision in the last block.
 cudaError_t launch_gemm_simt(int mode, int epi, const void* A, int64_t a_rows, const void* X,
                              int64_t np, void* out, const void* x_prev, Part3* part,
                              const Tile* tiles, int ntiles, const DevState* st, int step,
-                             cudaStream_t s);
+                             cudaStream_t s, const SimtDecide* dec = nullptr);
 void simt_tile_shape(int mode, int64_t np, int* bm, int* bn);
 
 // tcgen05 split-precision (BF16X2 / FP16X2 / BF16X3)
