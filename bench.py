@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--workload", default="chi",
                     choices=["chi", "fermi", "scf", "nonorth", "configs", "products", "sparse"])
     ap.add_argument("--tau", type=float, default=1e-5, help="block threshold of --workload sparse")
+    ap.add_argument("--only", default="all", choices=["all", "config1", "config2", "config3"],
+                    help="--workload configs: run one configuration only")
     ap.add_argument("--tiles", default="pair", choices=["pair", "single"],
                     help="product tiles: 256x256 on CTA pairs, or 128x256 on one SM")
     ap.add_argument("--scf-tol", type=float, default=1e-6)
@@ -915,88 +917,91 @@ def run_configs(args, ws, rank):
 
     out = {"config1": {}, "config2": {}, "config3": {}}
     # ---------------------------------------------------------------- config 1
-    p = workloads.random_spectrum(128, nocc=64, k=8, seed=0)
-    for mode, dt in (("fp64", torch.float64), ("fp16x2", torch.float32)):
-        H = torch.from_numpy(p.H).to(dt).cuda()
-        A = torch.from_numpy(p.A[None]).to(dt).cuda()
-        H1 = torch.from_numpy(p.H1).to(dt).cuda()
-        kw = dict(mode=mode, handle=h, idem_tol=1e-10 if mode == "fp64" else 0.0)
-        t_d, (_, inf) = timed(lambda: sp2.sp2_density(H, p.nocc, **kw), reps=20)
-        t_c, _ = timed(lambda: sp2.sp2_susceptibility(H, p.nocc, A, "backward", **kw), reps=20)
-        t_r, _ = timed(lambda: sp2.sp2_response(H, p.nocc, H1, **kw), reps=20)
-        m = inf["M"]
-        out["config1"][mode] = {"M": m, "density_ms": t_d, "density_us_per_iteration": 1e3 * t_d / m,
-                                "backward_chi_ms": t_c, "responses8_ms": t_r,
-                                "responses8_us_per_iteration": 1e3 * t_r / m}
+    if args.only in ("all", "config1"):
+        p = workloads.random_spectrum(128, nocc=64, k=8, seed=0)
+        for mode, dt in (("fp64", torch.float64), ("fp16x2", torch.float32)):
+            H = torch.from_numpy(p.H).to(dt).cuda()
+            A = torch.from_numpy(p.A[None]).to(dt).cuda()
+            H1 = torch.from_numpy(p.H1).to(dt).cuda()
+            kw = dict(mode=mode, handle=h, idem_tol=1e-10 if mode == "fp64" else 0.0)
+            t_d, (_, inf) = timed(lambda: sp2.sp2_density(H, p.nocc, **kw), reps=20)
+            t_c, _ = timed(lambda: sp2.sp2_susceptibility(H, p.nocc, A, "backward", **kw), reps=20)
+            t_r, _ = timed(lambda: sp2.sp2_response(H, p.nocc, H1, **kw), reps=20)
+            m = inf["M"]
+            out["config1"][mode] = {"M": m, "density_ms": t_d, "density_us_per_iteration": 1e3 * t_d / m,
+                                    "backward_chi_ms": t_c, "responses8_ms": t_r,
+                                    "responses8_us_per_iteration": 1e3 * t_r / m}
     # ---------------------------------------------------------------- config 2
-    tb = workloads.tight_binding(4096, seed=0, dtype=np.float32)
-    A4 = workloads.tb_dipole_observables(tb)                  # (4, N) diagonals
-    v = workloads.tb_site_potentials(tb, 64, seed=1)         # (64, N) diagonals
-    for mode, dt in (("fp16x2", torch.float32), ("fp32", torch.float32), ("fp64", torch.float64)):
-        H = torch.from_numpy(tb.H).to(dt).cuda()
-        Ad = torch.from_numpy(A4).to(dt).cuda()
-        vd = torch.from_numpy(v).to(dt).cuda()
-        if mode != "fp64":
-            def primal():
-                D1, _, inf = sp2.sp2_response(H, tb.nocc, vd, diag_only=True, mode=mode, handle=h)
-                return sp2.response_contract(D1, Ad, diag_only=True, handle=h), inf
-            def dual():
-                chi, _, inf = sp2.sp2_susceptibility(H, tb.nocc, Ad, "backward", diag_only=True,
-                                                     mode=mode, handle=h)
-                return sp2.response_contract(chi, vd, diag_only=True, handle=h), inf
-            t_p, (a_p, inf_p) = timed(primal)
-            t_q, (a_q, inf_q) = timed(dual)
-            a_p = a_p.cpu().numpy().T      # (4, 64)
-            a_q = a_q.cpu().numpy()
-            out["config2"][mode] = {"M": inf_q["M"], "primal_ms": t_p, "dual_ms": t_q,
-                                    "primal_over_dual": t_p / t_q,
-                                    "a1_primal_vs_dual": float(np.linalg.norm(a_p - a_q) / np.linalg.norm(a_q))}
-        else:
-            # one square and one 64-response step (fixed branch), event-timed, times the
-            # product counts of this mode's converged run (M from a density solve)
-            _, inf_d = sp2.sp2_density(H, tb.nocc, mode="fp64", idem_tol=1e-10, handle=h)
-            m = inf_d["M"]
-            _, inf_s = sp2.sp2_density(H, tb.nocc, mode="fp64", sigma=[1], time_kernels=True, handle=h)
-            _, _, inf_y = sp2.sp2_response(H, tb.nocc, vd, diag_only=True, mode="fp64", sigma=[1],
-                                           time_kernels=True, handle=h)
-            _, _, inf_a = sp2.sp2_susceptibility(H, tb.nocc, Ad, "forward", diag_only=True,
-                                                 mode="fp64", sigma=[1], time_kernels=True, handle=h)
-            sq = inf_s["product_ms"]
-            y64 = inf_y["product_ms"] - sq
-            y4 = inf_a["product_ms"] - sq
-            rec = m - (m + 3) // 4
-            out["config2"][mode] = {"M": m, "primal_ms_extrapolated": m * (sq + y64),
-                                    "dual_ms_extrapolated": (m + rec) * sq + m * y4,
-                                    "primal_over_dual": m * (sq + y64) / ((m + rec) * sq + m * y4),
-                                    "note": "per-product event times x product counts"}
-        del H
+    if args.only in ("all", "config2"):
+        tb = workloads.tight_binding(4096, seed=0, dtype=np.float32)
+        A4 = workloads.tb_dipole_observables(tb)                  # (4, N) diagonals
+        v = workloads.tb_site_potentials(tb, 64, seed=1)         # (64, N) diagonals
+        for mode, dt in (("fp16x2", torch.float32), ("fp32", torch.float32), ("fp64", torch.float64)):
+            H = torch.from_numpy(tb.H).to(dt).cuda()
+            Ad = torch.from_numpy(A4).to(dt).cuda()
+            vd = torch.from_numpy(v).to(dt).cuda()
+            if mode != "fp64":
+                def primal():
+                    D1, _, inf = sp2.sp2_response(H, tb.nocc, vd, diag_only=True, mode=mode, handle=h)
+                    return sp2.response_contract(D1, Ad, diag_only=True, handle=h), inf
+                def dual():
+                    chi, _, inf = sp2.sp2_susceptibility(H, tb.nocc, Ad, "backward", diag_only=True,
+                                                         mode=mode, handle=h)
+                    return sp2.response_contract(chi, vd, diag_only=True, handle=h), inf
+                t_p, (a_p, inf_p) = timed(primal)
+                t_q, (a_q, inf_q) = timed(dual)
+                a_p = a_p.cpu().numpy().T      # (4, 64)
+                a_q = a_q.cpu().numpy()
+                out["config2"][mode] = {"M": inf_q["M"], "primal_ms": t_p, "dual_ms": t_q,
+                                        "primal_over_dual": t_p / t_q,
+                                        "a1_primal_vs_dual": float(np.linalg.norm(a_p - a_q) / np.linalg.norm(a_q))}
+            else:
+                # one square and one 64-response step (fixed branch), event-timed, times the
+                # product counts of this mode's converged run (M from a density solve)
+                _, inf_d = sp2.sp2_density(H, tb.nocc, mode="fp64", idem_tol=1e-10, handle=h)
+                m = inf_d["M"]
+                _, inf_s = sp2.sp2_density(H, tb.nocc, mode="fp64", sigma=[1], time_kernels=True, handle=h)
+                _, _, inf_y = sp2.sp2_response(H, tb.nocc, vd, diag_only=True, mode="fp64", sigma=[1],
+                                               time_kernels=True, handle=h)
+                _, _, inf_a = sp2.sp2_susceptibility(H, tb.nocc, Ad, "forward", diag_only=True,
+                                                     mode="fp64", sigma=[1], time_kernels=True, handle=h)
+                sq = inf_s["product_ms"]
+                y64 = inf_y["product_ms"] - sq
+                y4 = inf_a["product_ms"] - sq
+                rec = m - (m + 3) // 4
+                out["config2"][mode] = {"M": m, "primal_ms_extrapolated": m * (sq + y64),
+                                        "dual_ms_extrapolated": (m + rec) * sq + m * y4,
+                                        "primal_over_dual": m * (sq + y64) / ((m + rec) * sq + m * y4),
+                                        "note": "per-product event times x product counts"}
+            del H
     # ---------------------------------------------------------------- config 3
-    n = 16384
-    tb3, A3 = workload(n, seed=0)
-    H = torch.from_numpy(tb3.H).cuda()
-    a = torch.from_numpy(A3[0]).cuda()
-    Ad = torch.from_numpy(A3).cuda()
-    hh = sp2.Handle()
+    if args.only in ("all", "config3"):
+        n = 16384
+        tb3, A3 = workload(n, seed=0)
+        H = torch.from_numpy(tb3.H).cuda()
+        a = torch.from_numpy(A3[0]).cuda()
+        Ad = torch.from_numpy(A3).cuda()
+        hh = sp2.Handle()
 
-    def via_autograd():
-        Hg = H.clone().requires_grad_(True)
-        D = sp2.sp2_density_autograd(Hg, tb3.nocc, mode="fp16x2", ckpt_k=4, handle=hh)
-        loss = (D.diagonal() * a).sum()          # Tr[A D], A the x-dipole
-        loss.backward()
-        return Hg.grad
+        def via_autograd():
+            Hg = H.clone().requires_grad_(True)
+            D = sp2.sp2_density_autograd(Hg, tb3.nocc, mode="fp16x2", ckpt_k=4, handle=hh)
+            loss = (D.diagonal() * a).sum()          # Tr[A D], A the x-dipole
+            loss.backward()
+            return Hg.grad
 
-    def direct():
-        chi, _, _ = sp2.sp2_susceptibility(H, tb3.nocc, Ad, "backward", diag_only=True,
-                                           mode="fp16x2", ckpt_k=4, handle=hh)
-        return chi[0]
+        def direct():
+            chi, _, _ = sp2.sp2_susceptibility(H, tb3.nocc, Ad, "backward", diag_only=True,
+                                               mode="fp16x2", ckpt_k=4, handle=hh)
+            return chi[0]
 
-    t_a, g = timed(via_autograd)
-    t_b, chi = timed(direct)
-    out["config3"] = {"autograd_ms": t_a, "direct_ms": t_b,
-                      "grad_vs_direct_chi_max_abs": float((g - chi).abs().max()),
-                      "chi_max_abs": float(chi.abs().max()),
-                      "note": "autograd: forward SP2 (keep_history, k=4), dense incoming gradient "
-                              "diag(A) of Tr[A D], adjoint (Eq. DM2); direct: the diagonal A"}
+        t_a, g = timed(via_autograd)
+        t_b, chi = timed(direct)
+        out["config3"] = {"autograd_ms": t_a, "direct_ms": t_b,
+                          "grad_vs_direct_chi_max_abs": float((g - chi).abs().max()),
+                          "chi_max_abs": float(chi.abs().max()),
+                          "note": "autograd: forward SP2 (keep_history, k=4), dense incoming gradient "
+                                  "diag(A) of Tr[A D], adjoint (Eq. DM2); direct: the diagonal A"}
     line = {"metric": "configs 1-3: N=128 us per SP2 iteration; N=4096 primal vs dual; "
                       "N=16384 autograd vs direct", "n_gpus": 1, "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
